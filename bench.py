@@ -1,0 +1,350 @@
+"""Benchmark of the DG-SWEM hot path on one GB300 (or N independent replicas under torchrun).
+
+Headline: element-stage updates/s of the FP64 form on the 199,712-element shelf workload
+(100 km x 50 km, 316x316 cells split by seeded diagonals, jittered, M2 tide on x = 0, wetting/
+drying with h0 = 0.01 m, quadratic friction, slope limiter; synthetic data).  One benchmark step
+= one SSP-RK2 time step (two stages) over the whole mesh.  The working set (~60 MB) is smaller
+than L2, so a 256 MB buffer is written between timed steps (outside the timed region).
+
+Also reported on one GPU: the FP32-mixed form at p = 1 and p = 2 on the same mesh, the FP64 form
+on the 3.2M-element storm domain, and the batched storm ensemble (64 scenarios on 4 meshes).
+
+--impl reference times the CPU oracle (tests' reference implementation, plain C, OpenMP build
+on all host cores) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "element-stage updates/s (FP64, 199,712-element shelf)"
+UNIT = "element-stage updates/s"
+NE_SHELF = 199712
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 arithmetic peak from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes/clock/SM x 2 flop x
+# 2.07 GHz (consistent with GB300's 1.25 TFLOP/s nominal dense FP64).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons, sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) > 8 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "common_kernels.cu", "api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2508_21208_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, form: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+    if not os.path.exists(p):
+        return None
+    sha = kernel_source_sha()
+    for line in open(p):
+        kv = dict(re.findall(r"(\w+)=(\S+)", line))
+        if kv.get("kernel") == kernel and kv.get("form") == form and kv.get("src_sha") == sha:
+            return float(kv["bytes"])
+    return None
+
+
+# ---------------------------------------------------------------- algorithmic cost per element-stage
+# Bytes the method must move per element-stage (neighbour traces assumed to come from L2):
+# state u^s read (9 x 8), u^n read on stage 2 (9 x 8 / 2), u^(s+1) written (9 x 8), element
+# statics (inverse Jacobian + det J + 3 vertex depths; 3 neighbour ids, 1 byte of local edges,
+# 1 wet/dry flag) and the edge statics x 1.5 edges per element (normal, length, 2 element ids,
+# 2 local ids).  FP64: 72 + 36 + 72 + 64 + 14 + 51 = 309 B.  Mixed: statics in float:
+# 72 + 36 + 72 + 32 + 14 + 33 = 259 B.  p = 2 adds 3 x 3 modes: FP64 453 B, mixed 403 B.
+ALG_BYTES = {("fp64", 1): 309, ("mixed", 1): 259, ("fp64", 2): 453, ("mixed", 2): 403}
+# FP64 flops per element-stage of the element-update kernel, counting each add, multiply, divide
+# and square root as one flop and an FMA as two (the paper's convention, Sec. 6.2), for the split
+# variant at p = 1: area integrals 6 points x 46 + 40, 3 local edges x (2 points x 18 + 12) and
+# update 9 x 6 (the edge kernel's share is counted on the edge kernel: 2 points x 86 per edge).
+ALG_FLOPS_ELEMENT_P1 = 6 * 46 + 40 + 3 * (2 * 18 + 12) + 9 * 6
+ALG_FLOPS_EDGE_P1 = 2 * 86
+
+
+def make_model(case, stream, **kw):
+    from paper_2508_21208_gb300 import Model
+    return Model(case.mesh, case.bathy, case.params, init_nodal=case.init_nodal, stream=stream, **kw)
+
+
+def time_steps(model, steps, warmup, stream, flush, per_kernel=False):
+    """Per-step CUDA-event timing on the library's stream, L2 flushed between steps."""
+    import torch
+    for _ in range(warmup):
+        model.step(1)
+    model.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kt = {}
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        model.step(1)
+        ev[i][1].record(stream)
+        if per_kernel:
+            stream.synchronize()
+            for name, ms in model.kernel_times():
+                kt.setdefault(name, []).append(ms)
+    stream.synchronize()
+    model.sync()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, kt
+
+
+def run_form(case, steps, warmup, stream, flush, per_kernel=True, **kw):
+    m = make_model(case, stream, **kw)
+    if per_kernel:
+        m.set_kernel_timing(True)
+    ms, kt = time_steps(m, steps, warmup, stream, flush, per_kernel)
+    kps, variant, block = m.graph_info()
+    return m, ms, kt, (kps, variant, block)
+
+
+def dominant(kt):
+    tot = {k: sum(v) for k, v in kt.items()}
+    name = max(tot, key=tot.get)
+    return name, statistics.mean(kt[name]) * 1e-3, tot
+
+
+def cpu_baseline(case, budget_s=12.0):
+    """The oracle as it stands (OpenMP build, all host cores), a bounded number of steps."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    o = oracle.Oracle(case.mesh, case.bathy, case.params, init_nodal=case.init_nodal, omp=True)
+    o.step(1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and n < 400:
+        o.step(1)
+        n += 1
+    el = time.perf_counter() - t0
+    return {"value": case.mesh.n_elems * 2 * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} SSP-RK2 steps of the full 199,712-element shelf workload ({el:.1f} s, OpenMP build)"}
+
+
+def e2e(case, steps, stream):
+    """Same metric through the C ABI with pinned host buffers: per step the state is copied host ->
+    device (dgswem_set_state), one step runs, and the state is copied back (dgswem_get_state)."""
+    import torch
+    m = make_model(case, stream)
+    u = m.state()
+    host = [torch.from_numpy(np.ascontiguousarray(u[v])).pin_memory() for v in range(3)]
+    outs = [torch.empty_like(h).pin_memory() for h in host]
+    hp = [h.numpy() for h in host]
+    op = [o.numpy() for o in outs]
+    for _ in range(3):
+        m.set_state_from(hp[0], hp[1], hp[2], 0.0)
+        m.step(1)
+        m.get_state_into(op[0], op[1], op[2])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        m.set_state_from(hp[0], hp[1], hp[2], 0.0)
+        m.step(1)
+        m.get_state_into(op[0], op[1], op[2])
+    el = time.perf_counter() - t0
+    nbytes = 3 * u.shape[1] * u.shape[2] * 8
+    return {"value": case.mesh.n_elems * 2 * steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes}
+
+
+def reference_arm(args, rank):
+    """--impl reference: the CPU oracle on the same workload, K timed steps after W warm-up."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2508_21208_gb300 import synth
+    case = synth.config2()
+    cores = len(os.sched_getaffinity(0))
+    o = oracle.Oracle(case.mesh, case.bathy, case.params, init_nodal=case.init_nodal, omp=True)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    v = NE_SHELF * 2 * args.steps / el
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "shelf-199712 (316x316 cells, tide, wet/dry, limiter, FP64, p=1)",
+                       "global_batch": NE_SHELF, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} SSP-RK2 steps of the full workload, OpenMP build"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    from paper_2508_21208_gb300 import synth
+    from paper_2508_21208_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    case = synth.config2()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        model, ms, kt, (kps, variant, block) = run_form(case, args.steps, args.warmup, stream, flush)
+    torch.cuda.synchronize()
+    total_s = sum(ms) * 1e-3
+    if dist:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    units = case.mesh.n_elems * 2 * args.steps * world
+    value = units / total_s
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    hbm, hbm_kind = peaks()
+    name, avg_s, tot = dominant(kt)
+    ne = case.mesh.n_elems
+    if name == "element_update":
+        flops = ALG_FLOPS_ELEMENT_P1 * ne
+    elif name == "edge_flux":
+        flops = ALG_FLOPS_EDGE_P1 * 1.5 * ne
+    else:
+        flops = None
+    roof = {"kernel": name, "bound": "alu", "unit": "GFLOP/s",
+            "achieved": flops / avg_s / 1e9 if flops else None, "peak": FP64_PEAK_GFLOPS,
+            "peak_kind": "derived from unit counts and clocks (FP64)",
+            "frac": (flops / avg_s / 1e9) / FP64_PEAK_GFLOPS if flops else None,
+            "traffic": recorded_traffic(name, "fp64"),
+            "avg_launch_ms": avg_s * 1e3, "launches_per_step": 2,
+            "share_of_step": tot[name] / sum(tot.values())}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "shelf-199712 (316x316 cells, tide, wet/dry, limiter, FP64, p=1)",
+                       "global_batch": ne * world, "parallelism": f"replicas x{world}",
+                       "l2": "256 MB buffer written between timed steps", "variant": variant,
+                       "block": block},
+            "gpu_launches": kps * args.steps,
+            "hbm_gbs_algorithmic": ALG_BYTES[("fp64", 1)] * value / world / 1e9,
+            "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
+            "roofline": roof,
+            "kernel_ms_per_step": {k: sum(v) / len(v) for k, v in kt.items()},
+            "clocks": clk.summary()}
+    if world == 1:
+        line["e2e"] = e2e(case, max(10, args.steps // 4), stream)
+        if not args.no_extras:
+            line["forms"] = extras(stream, flush, hbm)
+        line["cpu_baseline"] = cpu_baseline(case)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def extras(stream, flush, hbm):
+    """FP32-mixed (p = 1, 2), FP64 on the 3.2M-element storm domain; 20 timed steps each."""
+    from paper_2508_21208_gb300 import synth
+    out = {}
+    for key, case, form, p in (("fp32_mixed_p1", synth.config2(precision=synth.FP32_MIXED), "mixed", 1),
+                               ("fp32_mixed_p2", synth.config2(p=2, precision=synth.FP32_MIXED), "mixed", 2),
+                               ("fp64_storm_3.2M", synth.config3(), "fp64", 1)):
+        m, ms, kt, (kps, variant, block) = run_form(case, 20, 3, stream, flush)
+        rate = case.mesh.n_elems * 2 * 20 / (sum(ms) * 1e-3)
+        name, avg_s, tot = dominant(kt)
+        gbs = ALG_BYTES[(form, p)] * rate / 1e9
+        out[key] = {"value": rate, "unit": UNIT, "elements": case.mesh.n_elems, "ms_per_step": sum(ms) / 20,
+                    "variant": variant, "block": block, "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm,
+                    "dominant_kernel": name, "kernel_ms_per_step": {k: sum(v) / len(v) for k, v in kt.items()}}
+        del m
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * dgswem.h -- C ABI of the GB300 DG-SWEM hot path (libdgswem.so).
+ *
+ * The library advances the p-th order modal discontinuous Galerkin discretisation of the 2D
+ * shallow water equations (Wichitrnithed et al., arXiv 2508.21208, Sec. 2.1 Eq. SWE and
+ * Sec. 2.2 Eq. elem_weak_form / Eq. RKSSP) on an unstructured triangle mesh on one GPU:
+ * area integrals of flux and sources (Alg. 1), interior, land and open-ocean edge fluxes
+ * (Alg. 2, Alg. 3), the inverse (diagonal) mass matrix and the SSP-RK2 stage update, the slope
+ * limiter and the wetting/drying treatment (Sec. 5.2.3 SLOPELIM, WETDRY), and nodal wind /
+ * pressure forcing (Sec. 5.2.3 WIND).  Every step runs in CUDA kernels built for sm_103a; there
+ * is no CPU fallback.  Host code only preprocesses the mesh (edge list, neighbour maps, limiter
+ * geometry, locality reordering) and marshals arguments.
+ *
+ * Conventions (all entry points):
+ *  - Return 0 on success or a negative DGSWEM_E* code.  Errors are sticky per context; the text
+ *    of the first one is available from dgswem_last_error().
+ *  - Pointers named h_* / plain const pointers are HOST memory owned by the caller and only read
+ *    during the call (create deep-copies them).  The one device buffer the library uses is the
+ *    workspace the caller attaches (dgswem_attach); the library allocates no device memory.
+ *  - Modal state arrays are [ndof][n_elems] per variable (zeta, q_x = H u_x, q_y = H u_y),
+ *    modes in the order (0,0), (1,0), (0,1), (2,0), (1,1), (0,2) of the Dubiner basis
+ *    (Sec. 2.2, Eq. dubiner), elements in the caller's original order.  Mode (0,0) is the
+ *    element mean.  ndof = 3 at p = 1 and 6 at p = 2.
+ *  - Work is issued asynchronously on the CUDA stream given to dgswem_attach; calls that return
+ *    data to the host synchronise that stream.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef DGSWEM_H
+#define DGSWEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DGSWEM_API __attribute__((visibility("default")))
+#else
+#define DGSWEM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DGSWEM_OK 0
+#define DGSWEM_EINVAL -1     /* bad argument or parameter value */
+#define DGSWEM_EMESH -2      /* invalid mesh: index out of range, clockwise or degenerate
+                                triangle, edge shared by more than two triangles or by two
+                                triangles with the same orientation, boundary edge list entry
+                                that is not a boundary edge */
+#define DGSWEM_ECUDA -3      /* a CUDA runtime call failed */
+#define DGSWEM_ENONFINITE -4 /* a NaN or Inf appeared in the state */
+#define DGSWEM_ENEGDEPTH -5  /* an element mean depth became negative after wetting/drying */
+#define DGSWEM_ETIMEOUT -6   /* a bounded device-side wait gave up (ensemble grid barrier) */
+#define DGSWEM_ENOMEM -7     /* the attached workspace is smaller than dgswem_workspace_size */
+#define DGSWEM_ESTATE -8     /* call out of order (e.g. step before attach) */
+
+/* boundary edge types (Sec. 2.1: Gamma_land, Gamma_ocean) */
+#define DGSWEM_BC_LAND 0 /* no normal flow: mirror ghost state */
+#define DGSWEM_BC_OPEN 1 /* elevation-specified (tidal) boundary, momentum from the interior */
+
+/* arithmetic forms */
+#define DGSWEM_FP64 0       /* every step in IEEE double */
+#define DGSWEM_FP32_MIXED 1 /* volume, edge and source arithmetic in float; RK state, the RK
+                               update, the mass sum and the wet/dry depth tests in double */
+
+/* bottom friction tau_b (Eq. SWE) */
+#define DGSWEM_FRICTION_NONE 0
+#define DGSWEM_FRICTION_MANNING 1   /* tau_b = g n^2 |q| / H^(7/3) */
+#define DGSWEM_FRICTION_QUADRATIC 2 /* tau_b = C_f |q| / H^2 */
+
+/* kernel organisation of one RK stage (chosen by the autotuner when 0) */
+#define DGSWEM_VARIANT_AUTO 0
+#define DGSWEM_VARIANT_SPLIT 1 /* edge kernel stores each interior edge flux once, the element
+                                  kernel gathers it (the paper's Alg. 2 + Alg. 3 organisation,
+                                  atomic-free) */
+#define DGSWEM_VARIANT_FUSED 2 /* one element kernel computes its own edge fluxes from its
+                                  neighbours' states (no flux scratch, edge work done twice) */
+
+typedef struct dgswem_ctx dgswem_ctx; /* opaque, library-owned */
+
+/* Triangle mesh.  xy: [n_nodes][2] metres; tri: [n_elems][3] node indices, counter-clockwise,
+ * 0-based; bedge: [n_bedges][2] node pairs of boundary edges with bedge_type[n_bedges]
+ * (DGSWEM_BC_*).  Boundary edges absent from bedge are land. */
+typedef struct {
+  int32_t n_nodes, n_elems, n_bedges;
+  const double *xy;
+  const int32_t *tri;
+  const int32_t *bedge;
+  const int32_t *bedge_type;
+} dgswem_mesh;
+
+/* Model and numerics parameters (SI units). */
+typedef struct {
+  int32_t p;         /* polynomial degree: 1 or 2 (Sec. 2.2, Eq. dubiner) */
+  int32_t precision; /* DGSWEM_FP64 or DGSWEM_FP32_MIXED */
+  double g;          /* gravity */
+  double cfl;        /* dt = cfl * 3/(2p+1) * min_e r_e / lambda_e (r_e inradius) unless dt > 0 */
+  double dt;         /* > 0: fixed time step overriding cfl */
+  double h0;         /* wetting/drying minimum depth; 0 disables wetting/drying */
+  int32_t friction;  /* DGSWEM_FRICTION_* */
+  double manning_n, cf;
+  int32_t limiter;   /* 1: Cockburn-Shu minmod slope limiter after each stage */
+  int32_t coriolis;  /* 1: f = 2 Omega sin(latitude) Coriolis source */
+  double coriolis_lat_deg;
+  double tide_amp, tide_period, tide_phase; /* open boundary zeta = A sin(2 pi t / T + phase) */
+  int32_t hurricane; /* 1: Holland vortex wind stress and pressure gradient */
+  double pc_hpa, pn_hpa, rmax_m, holland_b, vt_ms, track_x0, track_y0, track_heading;
+  double rho_air, rho_water;
+} dgswem_params;
+
+/* Tuning knobs; pass NULL to dgswem_create for the defaults (all zero = automatic). */
+typedef struct {
+  int32_t variant;   /* DGSWEM_VARIANT_* */
+  int32_t block;     /* threads per block of the element kernels: 0 (auto), 64, 128, 256 */
+  int32_t reorder;   /* 0: auto (Hilbert order on), 1: Hilbert curve order, 2: keep caller order */
+  int32_t autotune;  /* 1: time the candidate variants / block sizes at attach and keep the best */
+} dgswem_tuning;
+
+/* Initial state: modal ([3][ndof][n_elems], caller order) or nodal ([3][n_nodes]: the linear
+ * interpolant in each element); both NULL = lake at rest (zeta = q = 0).  t0 is the start time. */
+typedef struct {
+  const double *modal;
+  const double *nodal;
+  double t0;
+} dgswem_init;
+
+/* Validate the mesh and parameters, preprocess the mesh on the host (edge list, neighbour and
+ * element-to-edge maps, boundary tags, limiter geometry, Hilbert-order relabelling) and keep a
+ * private copy of everything.  No device work happens here.  bathy: [n_nodes] h_b, positive
+ * downward (Sec. 2.1), linear within each element.  tuning may be NULL.
+ * Errors: DGSWEM_EINVAL, DGSWEM_EMESH; *out is set to NULL on error. */
+DGSWEM_API int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_params *params,
+                  const dgswem_init *init, const dgswem_tuning *tuning, dgswem_ctx **out);
+
+/* Bytes of device workspace (256-byte aligned) that dgswem_attach needs. */
+DGSWEM_API int dgswem_workspace_size(const dgswem_ctx *ctx, size_t *bytes);
+
+/* Bind a caller-owned device buffer of at least dgswem_workspace_size bytes (the caller keeps
+ * ownership and must keep it alive until dgswem_destroy) and a CUDA stream (cudaStream_t passed
+ * as void*; NULL = a private non-blocking stream the library creates).  Uploads the static mesh
+ * data and the initial state,
+ * applies the wetting/drying operator to the initial state, computes dt when params->dt <= 0,
+ * autotunes if asked, and captures one time step as a CUDA graph.  Synchronises the stream.
+ * Errors: DGSWEM_ENOMEM, DGSWEM_ECUDA, DGSWEM_ESTATE (already attached). */
+DGSWEM_API int dgswem_attach(dgswem_ctx *ctx, void *d_workspace, size_t bytes, void *stream);
+
+/* Advance n_steps SSP-RK2 time steps (two stages each, Sec. 2.2 Eq. RKSSP) by replaying the
+ * captured graph.  Asynchronous: device-side errors (DGSWEM_ENONFINITE, DGSWEM_ENEGDEPTH) are
+ * reported by the next synchronising call. */
+DGSWEM_API int dgswem_step(dgswem_ctx *ctx, int32_t n_steps);
+
+/* Copy the modal state to caller-owned host arrays, each [ndof][n_elems] in the caller's
+ * element order.  Any of the three pointers may be NULL.  Synchronises. */
+DGSWEM_API int dgswem_get_state(dgswem_ctx *ctx, double *h_zeta, double *h_qx, double *h_qy);
+
+/* Replace the modal state (caller order, same layout as dgswem_get_state) and set the time to t
+ * (the step counter restarts at 0).  Wet/dry flags are recomputed from the new state.  The
+ * copies are asynchronous; the host arrays must stay valid until the next synchronising call. */
+DGSWEM_API int dgswem_set_state(dgswem_ctx *ctx, const double *h_zeta, const double *h_qx,
+                     const double *h_qy, double t);
+
+/* Total surface anomaly volume sum_e |Omega_e| zeta_e,00 and water volume
+ * sum_e |Omega_e| (zeta_e,00 + mean h_b), each a compensated (Neumaier) double sum in a fixed
+ * block order, hence bitwise reproducible.  Synchronises. */
+DGSWEM_API int dgswem_mass(dgswem_ctx *ctx, double *mass_zeta, double *volume);
+
+/* Time step, current time t0 + steps*dt, and steps done since create / set_state. */
+DGSWEM_API int dgswem_info(dgswem_ctx *ctx, double *dt, double *t, int64_t *steps_done);
+
+/* Wait for the stream and surface any device-side error.  */
+DGSWEM_API int dgswem_sync(dgswem_ctx *ctx);
+
+/* Per-element wet/dry flags (0 wet, 1 partially wet, 2 dry), caller order.  Synchronises. */
+DGSWEM_API int dgswem_get_flags(dgswem_ctx *ctx, uint8_t *h_flags);
+
+DGSWEM_API void dgswem_destroy(dgswem_ctx *ctx);
+DGSWEM_API const char *dgswem_last_error(const dgswem_ctx *ctx);
+
+/* ---- single operators, for checking each step of the path against a reference ----
+ * Each runs the named kernel(s) once on the current state, on the context's stream, then
+ * synchronises. */
+
+/* L_h(u) of Eq. RKSSP at time t (area integrals, edge fluxes, inverse mass matrix; no limiter,
+ * no wet/dry), written to h_out as [3][ndof][n_elems] in caller order. */
+DGSWEM_API int dgswem_eval_rhs(dgswem_ctx *ctx, double t, double *h_out);
+/* Apply the slope limiter (SLOPELIM) to the current state in place. */
+DGSWEM_API int dgswem_apply_limiter(dgswem_ctx *ctx);
+/* Apply the wetting/drying operator (WETDRY) to the current state in place. */
+DGSWEM_API int dgswem_apply_wetdry(dgswem_ctx *ctx);
+/* Nodal forcing (WIND) at time t: h_out [3][n_nodes] = (tau_x/rho_w, tau_y/rho_w, p_a/rho_w). */
+DGSWEM_API int dgswem_eval_forcing(dgswem_ctx *ctx, double t, double *h_out);
+
+/* ---- kernel timing ----
+ * With timing on, the step graph is recaptured with event-record nodes between its kernels;
+ * dgswem_kernel_times then returns, for the last replayed step, each kernel's duration in
+ * milliseconds and its name (static strings), in launch order.  n_kernels gets the count. */
+DGSWEM_API int dgswem_set_kernel_timing(dgswem_ctx *ctx, int32_t on);
+DGSWEM_API int dgswem_kernel_times(dgswem_ctx *ctx, float *ms, const char **names, int32_t capacity,
+                        int32_t *n_kernels);
+/* Kernel launches per time step in the captured graph, and the chosen variant / block size. */
+DGSWEM_API int dgswem_graph_info(dgswem_ctx *ctx, int32_t *kernels_per_step, int32_t *variant,
+                      int32_t *block);
+
+/* ---- batched ensemble (several scenarios, meshes of uneven size) ----
+ * n members; member i uses meshes[i], bathy[i], params[i] and inits[i] (inits may be NULL).
+ * Members that pass the same mesh and bathymetry pointers share one copy of the static mesh
+ * data.  All members must use the same p and precision.  A step advances every member by one
+ * of its own time steps in one persistent cooperative kernel launch (grid barriers between the
+ * phases, each wait bounded in time), captured in a CUDA graph; tuning->block picks the
+ * element tile. */
+DGSWEM_API int dgswem_ensemble_create(int32_t n, const dgswem_mesh *const *meshes,
+                           const double *const *bathy, const dgswem_params *params,
+                           const dgswem_init *inits, const dgswem_tuning *tuning,
+                           dgswem_ctx **out);
+DGSWEM_API int dgswem_ensemble_get_state(dgswem_ctx *ctx, int32_t member, double *h_zeta, double *h_qx,
+                              double *h_qy);
+DGSWEM_API int dgswem_ensemble_info(dgswem_ctx *ctx, int32_t member, double *dt, double *t,
+                         int64_t *steps_done);
+/* Test hook: when on, one block skips every grid-barrier arrival, so the other blocks' bounded
+ * waits expire and the step reports DGSWEM_ETIMEOUT instead of hanging. */
+DGSWEM_API int dgswem_ensemble_set_fault(dgswem_ctx *ctx, int32_t skip_arrival);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGSWEM_H */

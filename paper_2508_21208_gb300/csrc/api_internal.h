@@ -1,0 +1,73 @@
+// api_internal.h -- the context behind the opaque dgswem_ctx handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct TuneEntry {
+  int variant, block;
+  float ms_per_step;
+};
+
+struct EnsembleState;  // ensemble.cu
+
+struct dgswem_ctx {
+  bool ensemble = false;
+  dgswem_params prm{};
+  dgswem_tuning tun{};
+  int P = 1, ND = 3;
+  bool mixed = false;
+  dg::HostMesh hm;
+  int init_kind = 0;  // 0 rest, 1 modal, 2 nodal
+  std::vector<double> init_modal, init_nodal;
+  double t0 = 0.0, dt = 0.0;
+  int64_t steps_done = 0;
+  // device side
+  size_t need = 0, ws_bytes = 0;
+  char *ws = nullptr;
+  cudaStream_t st = nullptr, own_stream = nullptr;
+  bool attached = false;
+  dg::DevMesh dm{};
+  dg::Phys ph{};
+  int *d_perm = nullptr, *d_iperm = nullptr;
+  double *U0 = nullptr, *U1 = nullptr, *mean = nullptr, *partial = nullptr, *result = nullptr,
+         *staging = nullptr;
+  uint8_t *wd = nullptr, *wd_stage = nullptr, *emode = nullptr;
+  void *eflux = nullptr, *frc = nullptr;
+  long long *step = nullptr;
+  int *err = nullptr;
+  unsigned long long *dtbits = nullptr;
+  void *h_pinned = nullptr;
+  int *h_err = nullptr;
+  double *h_res = nullptr;
+  std::vector<std::vector<char>> host_keep;
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernels_per_step = 0, variant = 0, block = 128;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<const char *> knames;
+  std::vector<TuneEntry> tune_log;
+  // errors
+  int sticky = 0;
+  std::string errmsg;
+  // ensemble
+  EnsembleState *ens = nullptr;
+};
+
+int ctx_fail(dgswem_ctx *c, int code, const std::string &msg);
+int ctx_cuda(dgswem_ctx *c, cudaError_t e, const char *what);
+int check_params(const dgswem_params *p, std::string &msg);
+dg::Phys make_phys(const dgswem_params &p);
+void upload_all_tables();
+int read_error_word(dgswem_ctx *c);
+int attach_common(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream);
+int capture_graph(dgswem_ctx *c, int variant, int block, bool timing);
+// ensemble.cu
+int ensemble_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream);
+void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names);
+void ensemble_release(dgswem_ctx *c);

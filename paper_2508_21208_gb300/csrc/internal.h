@@ -1,0 +1,186 @@
+// internal.h -- data structures shared by the host preprocessor, the C ABI and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgswem.h"
+
+namespace dg {
+
+constexpr int MAXD = 6;   // modes per variable at p <= 2
+constexpr int MAXQA = 12; // area quadrature points at p <= 2
+constexpr int MAXQE = 4;  // edge quadrature points at p <= 2
+
+__host__ __device__ constexpr int nd_of(int p) { return (p + 1) * (p + 2) / 2; }
+__host__ __device__ constexpr int nqa_of(int p) { return p == 1 ? 6 : 12; }
+__host__ __device__ constexpr int nqe_of(int p) { return p == 1 ? 2 : 4; }
+
+// Per-element geometry rows (structure of arrays, one row of n_elems values each).
+// J^{-1} = [[rx, ry], [sx, sy]] (d(xi,eta)/d(x,y)), det J = |Omega_e|/2, and for local edge l
+// (vertex (l+1)%3 -> (l+2)%3) the outward unit normal (nx_l, ny_l) and half length hl_l.
+enum {
+  GEO_RX, GEO_RY, GEO_SX, GEO_SY, GEO_DETJ,
+  GEO_NX0, GEO_NX1, GEO_NX2, GEO_NY0, GEO_NY1, GEO_NY2, GEO_HL0, GEO_HL1, GEO_HL2,
+  NGEO
+};
+
+constexpr int NBR_LAND = -1;
+constexpr int NBR_OPEN = -2;
+
+// Mesh after preprocessing, elements in internal (locality) order.
+struct HostMesh {
+  int ne = 0, nn = 0, nint = 0, nbnd = 0;
+  std::vector<int> perm;          // internal index -> caller index
+  std::vector<int> iperm;         // caller index -> internal index
+  std::vector<int> vnode;         // [3][ne] node ids
+  std::vector<double> geo;        // [NGEO][ne]
+  std::vector<double> hbv;        // [3][ne] vertex h_b
+  std::vector<double> area;       // [ne]
+  std::vector<double> inradius;   // [ne]
+  std::vector<int> nbr;           // [3][ne] neighbour (internal id) or NBR_LAND / NBR_OPEN
+  std::vector<uint8_t> nle;       // [ne] neighbour's local edge index, 2 bits per local edge
+  std::vector<int> eledge;        // [3][ne] interior edge id, bit 31 = this element is the minus side; -1
+  std::vector<double> lima;       // [3][2][ne] limiter weights
+  std::vector<uint16_t> limj;     // [ne] limiter neighbour pairs, 4 bits per local edge (15 = none)
+  std::vector<int> edel;          // [2][nint] (plus, minus) elements
+  std::vector<uint8_t> edle;      // [nint] l+ | l- << 2
+  std::vector<double> edgeo;      // [3][nint] nx, ny, half length (normal out of the plus side)
+  std::vector<double> edhb;       // [2][nint] h_b at the edge's end nodes (plus side's order)
+  std::vector<double> nodexy;     // [2][nn]
+};
+
+// Returns 0 or DGSWEM_EMESH / DGSWEM_EINVAL with a message.
+int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, HostMesh &out,
+                    std::string &msg);
+
+// ------------------------------------------------------------------ device-side views
+struct Phys {
+  double g, h0, cf, gn2, fcor;
+  double tide_amp, tide_omega, tide_phase;
+  double pc, pn, rmax, hB, vt, x0, y0, heading, flat, rho_air, rho_w;
+  int friction, wetdry, limiter, hurricane;
+};
+
+struct DevMesh {
+  int ne, nn, nint;
+  const void *geo;         // T [NGEO][ne]
+  const double *hbv;       // [3][ne]
+  const double *area;      // [ne]
+  const double *inradius;  // [ne]
+  const int *nbr;          // [3][ne]
+  const uint8_t *nle;      // [ne]
+  const int *vnode;        // [3][ne]
+  const void *lima;        // T [6][ne]
+  const uint16_t *limj;    // [ne]
+  const int *eledge;       // [3][ne]
+  const int *edel;         // [2][nint]
+  const uint8_t *edle;     // [nint]
+  const void *edgeo;       // T [3][nint]
+  const double *edhb;      // [2][nint]
+  const double *nodexy;    // [2][nn]
+};
+
+struct Clock {
+  const long long *step;   // device counter of completed steps
+  double t0, dt;           // stage time = t0 + (step + stage) * dt
+};
+
+struct StageArgs {
+  const double *uin;       // u^(s): [3][ND][ne]
+  const double *un;        // u^n (second stage only)
+  double *uout;            // u^(s+1)
+  double *mean;            // [3][ne] element means of u^(s+1), read by the limiter
+  const uint8_t *wd;       // wet/dry flags
+  void *eflux;             // T [3][NQE][nint] weighted interior-edge fluxes (split variant)
+  uint8_t *emode;          // [nint] 1 = the edge flux in eflux applies, 0 = both sides see a wall
+  const void *frc;         // T [3][nn] nodal forcing at the stage time, or nullptr
+  Clock clk;
+  int stage;
+  int *err;
+  double tide_t;           // stage time when clk.step is null (single operator calls)
+};
+
+// error word bits
+constexpr int ERR_NONFINITE = 1;
+constexpr int ERR_NEGDEPTH = 2;
+constexpr int ERR_TIMEOUT = 4;
+
+// reference tables (product-side restatement of the basis and quadrature)
+template <typename T>
+struct Tab {
+  T wq[MAXQA];             // area weights on the reference triangle (area 2)
+  T phq[MAXQA][MAXD];      // basis at area points
+  T dxq[MAXQA][MAXD];      // d basis / d xi
+  T dyq[MAXQA][MAXD];      // d basis / d eta
+  T nq[MAXQA][3];          // linear vertex shape functions at area points
+  T we[MAXQE];             // edge weights on [-1, 1]
+  T se[MAXQE];             // edge points on [-1, 1] (ascending, mirror symmetric)
+  T phe[3][MAXQE][MAXD];   // basis on local edge l at its own parameter s_g
+  T nrm[MAXD];             // squared reference norms
+  T inrm[MAXD];            // their inverses
+  T phm[3][3];             // linear modes at the three edge midpoints
+  T phv[3][MAXD];          // basis at the three vertices
+};
+
+void build_tables(int p, Tab<double> &t);
+
+// launchers (kernels_f64.cu: T = double; kernels_f32.cu: T = float)
+struct LaunchCfg {
+  int block;
+  cudaStream_t stream;
+};
+#define DG_DECLARE_LAUNCHERS(SUF)                                                                 \
+  void upload_tables_##SUF(const Tab<double> td[2]);                                             \
+  void launch_forcing_##SUF(const DevMesh &m, const Phys &ph, const Clock &clk, int stage,       \
+                            double t_fixed, void *frc, const LaunchCfg &c);                      \
+  void launch_edge_##SUF(int p, const DevMesh &m, const StageArgs &s, const Phys &ph,            \
+                         const LaunchCfg &c);                                                    \
+  void launch_element_##SUF(int p, bool split, bool write_rhs, const DevMesh &m,                 \
+                            const StageArgs &s, const Phys &ph, const LaunchCfg &c);             \
+  void launch_limwd_##SUF(int p, bool do_lim, int do_wd, const DevMesh &m, double *u,            \
+                          const double *mean, uint8_t *wd, const Phys &ph, int *err,             \
+                          const LaunchCfg &c);
+DG_DECLARE_LAUNCHERS(f64)
+DG_DECLARE_LAUNCHERS(f32)
+#undef DG_DECLARE_LAUNCHERS
+
+inline void launch_forcing(bool mixed, const DevMesh &m, const Phys &ph, const Clock &clk, int stage,
+                           double t_fixed, void *frc, const LaunchCfg &c) {
+  mixed ? launch_forcing_f32(m, ph, clk, stage, t_fixed, frc, c)
+        : launch_forcing_f64(m, ph, clk, stage, t_fixed, frc, c);
+}
+inline void launch_edge(bool mixed, int p, const DevMesh &m, const StageArgs &s, const Phys &ph,
+                        const LaunchCfg &c) {
+  mixed ? launch_edge_f32(p, m, s, ph, c) : launch_edge_f64(p, m, s, ph, c);
+}
+inline void launch_element(bool mixed, int p, bool split, bool write_rhs, const DevMesh &m,
+                           const StageArgs &s, const Phys &ph, const LaunchCfg &c) {
+  mixed ? launch_element_f32(p, split, write_rhs, m, s, ph, c)
+        : launch_element_f64(p, split, write_rhs, m, s, ph, c);
+}
+inline void launch_limwd(bool mixed, int p, bool do_lim, int do_wd, const DevMesh &m, double *u,
+                         const double *mean, uint8_t *wd, const Phys &ph, int *err,
+                         const LaunchCfg &c) {
+  mixed ? launch_limwd_f32(p, do_lim, do_wd, m, u, mean, wd, ph, err, c)
+        : launch_limwd_f64(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
+}
+void upload_common_tables(const Tab<double> td[2]);
+
+// precision-independent kernels (common_kernels.cu)
+void launch_init_nodal(int p, const DevMesh &m, const double *nodal, double *u, cudaStream_t s);
+void launch_copy_means(int p, int ne, const double *u, double *mean, cudaStream_t s);
+void launch_dt(int p, const DevMesh &m, const double *u, const Phys &ph, unsigned long long *best,
+               cudaStream_t s);
+void launch_mass(int p, const DevMesh &m, const double *u, double *partial, double *result,
+                 cudaStream_t s);
+void launch_permute(const double *src, double *dst, const int *map, int rows, int ne,
+                    cudaStream_t s);
+void launch_permute_u8(const uint8_t *src, uint8_t *dst, const int *map, int ne, cudaStream_t s);
+void launch_advance(long long *step, cudaStream_t s);
+int mass_partial_count(int ne);
+
+}  // namespace dg

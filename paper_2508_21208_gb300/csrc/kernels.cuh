@@ -1,0 +1,661 @@
+// kernels.cuh -- device code of one RK stage: forcing (WIND), edge flux (EDGE), element update
+// (AREA + GATHER + inverse mass + SSP-RK2), slope limiter + wetting/drying (SLOPELIM, WETDRY).
+// Included by kernels_f64.cu (T = double: the FP64 form) and kernels_f32.cu (T = float: the
+// mixed form, where the RK state, the RK update and all wet/dry depth tests stay in double).
+#pragma once
+#include <cstdint>
+
+#include "internal.h"
+
+namespace dg {
+
+// Reference tables; each translation unit holds its own constant-memory copy.
+static __constant__ Tab<double> c_td[2];
+static __constant__ Tab<float> c_tf[2];
+
+template <typename T>
+__device__ __forceinline__ const Tab<T> &ctab(int p);
+template <>
+__device__ __forceinline__ const Tab<double> &ctab<double>(int p) { return c_td[p - 1]; }
+template <>
+__device__ __forceinline__ const Tab<float> &ctab<float>(int p) { return c_tf[p - 1]; }
+
+__device__ __forceinline__ double stage_time(const Clock &c, int stage, double fixed) {
+  return c.step ? c.t0 + (double)(*c.step + stage) * c.dt : fixed;
+}
+
+// ------------------------------------------------------------------------ point physics
+// Normal flux F(w).n of Eq. SWE with the pressure term (g/2)(H^2 - h_b^2) = (g/2) zeta (zeta + 2 h_b).
+template <typename T>
+struct Side {
+  T F[3];  // F(w).n
+  T s;     // |u.n| + sqrt(g H)
+};
+
+template <typename T>
+__device__ __forceinline__ Side<T> side_flux(T g, const T w[3], T hb, T nx, T ny) {
+  Side<T> r;
+  const T H = w[0] + hb;
+  const T qn = w[1] * nx + w[2] * ny;
+  const T un = qn / H;
+  const T P = T(0.5) * g * w[0] * (w[0] + T(2) * hb);
+  r.F[0] = qn;
+  r.F[1] = w[1] * un + P * nx;
+  r.F[2] = w[2] * un + P * ny;
+  r.s = fabs(un) + sqrt(g * (H > T(0) ? H : T(0)));
+  return r;
+}
+
+// Local Lax-Friedrichs flux (the numerical flux of Eq. elem_weak_form), n from wi to wo.
+template <typename T>
+__device__ __forceinline__ void llf(T g, const T wi[3], const T wo[3], T hb, T nx, T ny, T out[3]) {
+  const Side<T> a = side_flux(g, wi, hb, nx, ny);
+  const Side<T> b = side_flux(g, wo, hb, nx, ny);
+  const T lam = a.s > b.s ? a.s : b.s;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) out[v] = T(0.5) * (a.F[v] + b.F[v]) - T(0.5) * lam * (wo[v] - wi[v]);
+}
+
+// Land (no normal flow): mirror ghost zeta- = zeta+, q- = q+ - 2 (q+.n) n, then LLF.
+template <typename T>
+__device__ __forceinline__ void wall(T g, const T wi[3], T hb, T nx, T ny, T out[3]) {
+  const T qn = wi[1] * nx + wi[2] * ny;
+  const T wo[3] = {wi[0], wi[1] - T(2) * qn * nx, wi[2] - T(2) * qn * ny};
+  llf(g, wi, wo, hb, nx, ny, out);
+}
+
+template <typename T>
+__device__ __forceinline__ T friction_tau(const Phys &ph, T qx, T qy, T H, T iH) {
+  const T qm = sqrt(qx * qx + qy * qy);
+  if (ph.friction == DGSWEM_FRICTION_QUADRATIC) return (T)ph.cf * qm * iH * iH;
+  if (ph.friction == DGSWEM_FRICTION_MANNING) return (T)ph.gn2 * qm * iH * iH * rcbrt(H);
+  return T(0);
+}
+
+// Wetting/drying edge rule: an edge touching a dry element carries no flow (each side sees a
+// wall) unless the wet side's surface trace rises above the highest bed (-h_b) on the edge.
+// The depth test runs in double in both forms.
+template <int P>
+__device__ __forceinline__ bool edge_flows(const Phys &ph, uint8_t f_self, uint8_t f_nbr,
+                                           const double *u, int ne, int e_self, int l_self, int e_nbr,
+                                           int l_nbr, double hbA, double hbB) {
+  if (!ph.wetdry) return true;
+  const bool ds = f_self == 2, dn = f_nbr == 2;
+  if (!ds && !dn) return true;
+  if (ds && dn) return false;
+  constexpr int ND = nd_of(P), NQE = nqe_of(P);
+  const int ew = ds ? e_nbr : e_self, lw = ds ? l_nbr : l_self;
+  const Tab<double> &td = c_td[P - 1];
+  double zmax = -INFINITY;
+#pragma unroll
+  for (int g = 0; g < NQE; ++g) {
+    double z = 0.0;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) z += u[(size_t)k * ne + ew] * td.phe[lw][g][k];
+    zmax = z > zmax ? z : zmax;
+  }
+  const double bed = (-hbA > -hbB) ? -hbA : -hbB;
+  return zmax > bed;
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void load_modes(const double *u, int ne, int e, T w[3][nd_of(P)]) {
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int k = 0; k < nd_of(P); ++k) w[v][k] = (T)__ldg(&u[(size_t)(v * nd_of(P) + k) * ne + e]);
+}
+
+// ------------------------------------------------------------------------ WIND
+// Holland (1980) vortex: p = pc + (pn - pc) exp(-(Rmax/r)^B); gradient wind
+// V = sqrt(B/rho_a (pn - pc) (Rmax/r)^B exp(-(Rmax/r)^B) + (r f/2)^2) - r f/2; surface wind 0.9 V
+// counter-clockwise plus half the translation velocity; Garratt (1977) drag
+// C_d = min(0.75 + 0.067 |U|, 3.5) 1e-3.  Output per node: tau/rho_w (x, y) and the pressure
+// anomaly (p - pn)/rho_w (only its gradient enters the momentum source).
+template <typename T>
+__global__ void k_forcing(const double *nodexy, int nn, Phys ph, Clock clk, int stage, double t_fixed,
+                          T *frc) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const double t = stage_time(clk, stage, t_fixed);
+  const double ch = cos(ph.heading), sh = sin(ph.heading);
+  const T dx = (T)(nodexy[n] - (ph.x0 + ph.vt * ch * t));
+  const T dy = (T)(nodexy[nn + n] - (ph.y0 + ph.vt * sh * t));
+  const T r = sqrt(dx * dx + dy * dy);
+  const T dp = (T)(ph.pn - ph.pc);
+  const T tx = T(0.5) * (T)(ph.vt * ch), ty = T(0.5) * (T)(ph.vt * sh);
+  T pa, ux, uy;
+  if (r < T(1)) {
+    pa = -dp;
+    ux = tx;
+    uy = ty;
+  } else {
+    const T A = pow((T)ph.rmax / r, (T)ph.hB), E = exp(-A);
+    pa = -dp + dp * E;
+    const T hf = T(0.5) * r * (T)ph.flat;
+    const T V = sqrt((T)ph.hB / (T)ph.rho_air * dp * A * E + hf * hf) - hf;
+    ux = T(0.9) * V * (-dy / r) + tx;
+    uy = T(0.9) * V * (dx / r) + ty;
+  }
+  const T U = sqrt(ux * ux + uy * uy);
+  T cd = T(0.75) + T(0.067) * U;
+  cd = (cd > T(3.5) ? T(3.5) : cd) * T(1e-3);
+  const T k = (T)(ph.rho_air / ph.rho_w) * cd * U;
+  frc[n] = k * ux;
+  frc[nn + n] = k * uy;
+  frc[2 * nn + n] = pa / (T)ph.rho_w;
+}
+
+// ------------------------------------------------------------------------ EDGE (split variant)
+// One thread per interior edge: both traces at the edge Gauss points, the wet/dry flow decision,
+// the LLF flux, stored once per edge already multiplied by the quadrature weight and half length
+// (the minus side reads it with the opposite sign and reversed point order).
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s, const Phys ph) {
+  constexpr int ND = nd_of(P), NQE = nqe_of(P);
+  __shared__ T s_phe[3][NQE][ND];
+  const Tab<T> &tb = ctab<T>(P);
+  for (int i = threadIdx.x; i < 3 * NQE * ND; i += blockDim.x)
+    s_phe[i / (NQE * ND)][(i / ND) % NQE][i % ND] = tb.phe[i / (NQE * ND)][(i / ND) % NQE][i % ND];
+  __syncthreads();
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nint = m.nint, ne = m.ne;
+  if (d >= nint) return;
+  const int ep = m.edel[d], em = m.edel[nint + d];
+  const int code = m.edle[d], lp = code & 3, lm = code >> 2;
+  const T *eg = (const T *)m.edgeo;
+  const T nx = eg[d], ny = eg[nint + d], hl = eg[2 * nint + d];
+  const double hbA = m.edhb[d], hbB = m.edhb[nint + d];
+  const bool flows = edge_flows<P>(ph, s.wd ? s.wd[ep] : 0, s.wd ? s.wd[em] : 0, s.uin, ne, ep, lp,
+                                   em, lm, hbA, hbB);
+  s.emode[d] = flows ? 1 : 0;
+  if (!flows) return;
+  T wp[3][ND], wm[3][ND];
+  load_modes<P, T>(s.uin, ne, ep, wp);
+  load_modes<P, T>(s.uin, ne, em, wm);
+  const T g = (T)ph.g;
+  T *F = (T *)s.eflux;
+#pragma unroll
+  for (int q = 0; q < NQE; ++q) {
+    T a[3], b[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      T x = 0, y = 0;
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {
+        x += wp[v][k] * s_phe[lp][q][k];
+        y += wm[v][k] * s_phe[lm][NQE - 1 - q][k];
+      }
+      a[v] = x;
+      b[v] = y;
+    }
+    const T hb = T(0.5) * ((T(1) - tb.se[q]) * (T)hbA + (T(1) + tb.se[q]) * (T)hbB);
+    T f[3];
+    llf(g, a, b, hb, nx, ny, f);
+    const T wgt = hl * tb.we[q];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) F[(size_t)(v * NQE + q) * nint + d] = wgt * f[v];
+  }
+}
+
+// ------------------------------------------------------------------------ element update
+// One thread per element.  r_k = (grad phi_k, F)_e + (phi_k, s)_e - <phi_k, Fhat.n>_de
+// (Eq. elem_weak_form with the volume term's sign fixed by integration by parts, Alg. 1 and the
+// gather of Alg. 3), L_k = r_k / (|J| ||phi_k||^2), then the SSP-RK2 stage (Shu-Osher form):
+// stage 0: u1 = u + dt L(u); stage 1: u_new = u/2 + (u1 + dt L(u1))/2, in double.
+// Source terms linear in the state (bathymetry slope g zeta dh_b/dx, Coriolis, wind stress,
+// pressure gradient -H dp_a/dx with linear p_a) are integrated in closed form through the basis
+// orthogonality; the area rule is exact for them, so this is the same discrete operator.
+template <int P, typename T, bool SPLIT>
+__global__ void __launch_bounds__(256)
+    k_element(const DevMesh m, const StageArgs s, const Phys ph, const int write_rhs) {
+  constexpr int ND = nd_of(P), NQA = nqa_of(P), NQE = nqe_of(P);
+  __shared__ T s_phe[3][NQE][ND];
+  const Tab<T> &tb = ctab<T>(P);
+  for (int i = threadIdx.x; i < 3 * NQE * ND; i += blockDim.x)
+    s_phe[i / (NQE * ND)][(i / ND) % NQE][i % ND] = tb.phe[i / (NQE * ND)][(i / ND) % NQE][i % ND];
+  __syncthreads();
+  const int ne = m.ne;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const double ts = stage_time(s.clk, s.stage, s.tide_t);
+  const T g = (T)ph.g;
+  T w[3][ND];
+  load_modes<P, T>(s.uin, ne, e, w);
+  const T *geo = (const T *)m.geo;
+  const T rx = geo[GEO_RX * (size_t)ne + e], ry = geo[GEO_RY * (size_t)ne + e];
+  const T sx = geo[GEO_SX * (size_t)ne + e], sy = geo[GEO_SY * (size_t)ne + e];
+  const T dJ = geo[GEO_DETJ * (size_t)ne + e];
+  const double hbd[3] = {m.hbv[e], m.hbv[ne + e], m.hbv[2 * (size_t)ne + e]};
+  const T hb[3] = {(T)hbd[0], (T)hbd[1], (T)hbd[2]};
+  T r[3][ND];
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int k = 0; k < ND; ++k) r[v][k] = T(0);
+
+  // ---------------- area integrals (Alg. 1): advective + pressure flux and friction
+  {
+    T fr[2][ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) fr[0][k] = fr[1][k] = T(0);
+    T Gx = 0, Gy = 0, Hy = 0;  // P = 1: sums of w_q F at the points (grad phi is constant)
+#pragma unroll
+    for (int q = 0; q < NQA; ++q) {
+      T z = 0, qx = 0, qy = 0;
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {
+        z += w[0][k] * tb.phq[q][k];
+        qx += w[1][k] * tb.phq[q][k];
+        qy += w[2][k] * tb.phq[q][k];
+      }
+      const T hq = hb[0] * tb.nq[q][0] + hb[1] * tb.nq[q][1] + hb[2] * tb.nq[q][2];
+      const T H = z + hq;
+      const T iH = T(1) / H;
+      const T Pp = T(0.5) * g * z * (z + T(2) * hq);
+      const T u = qx * iH, v = qy * iH;
+      const T Fxx = qx * u + Pp, Fxy = qx * v, Fyy = qy * v + Pp;
+      const T wq = tb.wq[q];
+      if constexpr (P == 1) {
+        Gx += wq * Fxx;
+        Gy += wq * Fxy;
+        Hy += wq * Fyy;
+      } else {
+#pragma unroll
+        for (int k = 1; k < ND; ++k) {
+          const T gx = rx * tb.dxq[q][k] + sx * tb.dyq[q][k];
+          const T gy = ry * tb.dxq[q][k] + sy * tb.dyq[q][k];
+          r[0][k] += wq * (gx * qx + gy * qy);
+          r[1][k] += wq * (gx * Fxx + gy * Fxy);
+          r[2][k] += wq * (gx * Fxy + gy * Fyy);
+        }
+      }
+      if (ph.friction) {
+        const T tw = wq * friction_tau<T>(ph, qx, qy, H, iH);
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+          fr[0][k] += tw * qx * tb.phq[q][k];
+          fr[1][k] += tw * qy * tb.phq[q][k];
+        }
+      }
+    }
+    if constexpr (P == 1) {
+      // grad psi_10 = J^-T (1, 1/2), grad psi_01 = J^-T (0, 3/2); the mass flux q is linear, so
+      // sum_q w_q q(x_q) = 2 q_00 exactly
+      const T g1x = rx + T(0.5) * sx, g1y = ry + T(0.5) * sy;
+      const T g2x = T(1.5) * sx, g2y = T(1.5) * sy;
+      r[0][1] = T(2) * (g1x * w[1][0] + g1y * w[2][0]);
+      r[0][2] = T(2) * (g2x * w[1][0] + g2y * w[2][0]);
+      r[1][1] = g1x * Gx + g1y * Gy;
+      r[1][2] = g2x * Gx + g2y * Gy;
+      r[2][1] = g1x * Gy + g1y * Hy;
+      r[2][2] = g2x * Gy + g2y * Hy;
+    }
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      r[0][k] *= dJ;
+      r[1][k] = (r[1][k] - fr[0][k]) * dJ;
+      r[2][k] = (r[2][k] - fr[1][k]) * dJ;
+    }
+  }
+
+  // ---------------- edge integrals (Alg. 2 + Alg. 3), gathered per element in a fixed order
+  const uint8_t fe = s.wd ? s.wd[e] : 0;
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    const int j = m.nbr[(size_t)l * ne + e];
+    const T nx = geo[(GEO_NX0 + l) * (size_t)ne + e], ny = geo[(GEO_NY0 + l) * (size_t)ne + e];
+    const T hl = geo[(GEO_HL0 + l) * (size_t)ne + e];
+    // end-node bathymetry of local edge l (vertex (l+1)%3 -> (l+2)%3), selected without
+    // dynamic register indexing
+    const T hbA = l == 0 ? hb[1] : (l == 1 ? hb[2] : hb[0]);
+    const T hbB = l == 0 ? hb[2] : (l == 1 ? hb[0] : hb[1]);
+    const double hbAd = l == 0 ? hbd[1] : (l == 1 ? hbd[2] : hbd[0]);
+    const double hbBd = l == 0 ? hbd[2] : (l == 1 ? hbd[0] : hbd[1]);
+    T wp[NQE][3], hbq[NQE], Fh[NQE][3];
+#pragma unroll
+    for (int q = 0; q < NQE; ++q) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        T x = 0;
+#pragma unroll
+        for (int k = 0; k < ND; ++k) x += w[v][k] * s_phe[l][q][k];
+        wp[q][v] = x;
+      }
+      hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hbA + (T(1) + tb.se[q]) * hbB);
+    }
+    bool weighted = false;  // Fh already carries hl * w_q
+    if (j >= 0) {
+      bool flows;
+      if constexpr (SPLIT) {
+        const int ed = m.eledge[(size_t)l * ne + e];
+        const bool minus = ed < 0;
+        const int id = ed & 0x7fffffff;
+        flows = s.emode[id] != 0;
+        if (flows) {
+          weighted = true;
+          const T *F = (const T *)s.eflux;
+#pragma unroll
+          for (int q = 0; q < NQE; ++q) {
+            const int qi = minus ? NQE - 1 - q : q;
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+              const T f = F[(size_t)(v * NQE + qi) * m.nint + id];
+              Fh[q][v] = minus ? -f : f;
+            }
+          }
+        }
+      } else {
+        const int lj = (m.nle[e] >> (2 * l)) & 3;
+        flows = edge_flows<P>(ph, fe, s.wd ? s.wd[j] : 0, s.uin, ne, e, l, j, lj, hbAd, hbBd);
+        if (flows) {
+          T wn[3][ND];
+          load_modes<P, T>(s.uin, ne, j, wn);
+#pragma unroll
+          for (int q = 0; q < NQE; ++q) {
+            T wm[3];
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+              T x = 0;
+#pragma unroll
+              for (int k = 0; k < ND; ++k) x += wn[v][k] * s_phe[lj][NQE - 1 - q][k];
+              wm[v] = x;
+            }
+            llf(g, wp[q], wm, hbq[q], nx, ny, Fh[q]);
+          }
+        }
+      }
+      if (!flows)
+#pragma unroll
+        for (int q = 0; q < NQE; ++q) wall(g, wp[q], hbq[q], nx, ny, Fh[q]);
+    } else if (j == NBR_LAND) {
+#pragma unroll
+      for (int q = 0; q < NQE; ++q) wall(g, wp[q], hbq[q], nx, ny, Fh[q]);
+    } else {
+      const T zt = (T)(ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase));
+#pragma unroll
+      for (int q = 0; q < NQE; ++q) {
+        const T wo[3] = {zt, wp[q][1], wp[q][2]};
+        llf(g, wp[q], wo, hbq[q], nx, ny, Fh[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NQE; ++q) {
+      const T wgt = weighted ? T(1) : hl * tb.we[q];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const T f = wgt * Fh[q][v];
+#pragma unroll
+        for (int k = 0; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
+      }
+    }
+  }
+
+  // ---------------- inverse mass matrix, closed-form linear sources, RK stage
+  const T idJ = T(1) / dJ;
+  T src1[3] = {0, 0, 0}, src2[3] = {0, 0, 0};  // per linear mode, for q_x and q_y
+  {
+    const T hbx = T(0.5) * (rx * (hb[1] - hb[0]) + sx * (hb[2] - hb[0]));
+    const T hby = T(0.5) * (ry * (hb[1] - hb[0]) + sy * (hb[2] - hb[0]));
+    const T fc = (T)ph.fcor;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      src1[k] = g * hbx * w[0][k] + fc * w[2][k];
+      src2[k] = g * hby * w[0][k] - fc * w[1][k];
+    }
+    if (s.frc) {
+      const T *F = (const T *)s.frc;
+      const int nn = m.nn;
+      const int n0 = m.vnode[e], n1 = m.vnode[ne + e], n2 = m.vnode[2 * (size_t)ne + e];
+      const T t0 = F[n0], t1 = F[n1], t2 = F[n2];
+      const T u0 = F[nn + n0], u1 = F[nn + n1], u2 = F[nn + n2];
+      const T p0 = F[2 * nn + n0], p1 = F[2 * nn + n1], p2 = F[2 * nn + n2];
+      const T pax = T(0.5) * (rx * (p1 - p0) + sx * (p2 - p0));
+      const T pay = T(0.5) * (ry * (p1 - p0) + sy * (p2 - p0));
+      // Dubiner linear modes of the interpolant through vertex values (a0, a1, a2)
+      const T hm[3] = {(hb[0] + hb[1] + hb[2]) / T(3), T(0.5) * (hb[1] - hb[0]),
+                       (T(2) * hb[2] - hb[0] - hb[1]) / T(6)};
+      const T tm[3] = {(t0 + t1 + t2) / T(3), T(0.5) * (t1 - t0), (T(2) * t2 - t0 - t1) / T(6)};
+      const T um[3] = {(u0 + u1 + u2) / T(3), T(0.5) * (u1 - u0), (T(2) * u2 - u0 - u1) / T(6)};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        src1[k] += tm[k] - pax * (w[0][k] + hm[k]);
+        src2[k] += um[k] - pay * (w[0][k] + hm[k]);
+      }
+      if constexpr (P == 2) {
+        // quadratic modes: only the zeta part of -H grad p_a remains
+        for (int k = 3; k < ND; ++k) {
+          r[1][k] -= dJ * tb.nrm[k] * pax * w[0][k];
+          r[2][k] -= dJ * tb.nrm[k] * pay * w[0][k];
+        }
+      }
+    }
+    if constexpr (P == 2) {
+      for (int k = 3; k < ND; ++k) {
+        r[1][k] += dJ * tb.nrm[k] * (g * hbx * w[0][k] + fc * w[2][k]);
+        r[2][k] += dJ * tb.nrm[k] * (g * hby * w[0][k] - fc * w[1][k]);
+      }
+    }
+  }
+  const double dt = s.clk.dt;
+  const size_t base = (size_t)ne;
+  bool bad = false;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      T L = r[v][k] * idJ * tb.inrm[k];
+      if (k < 3) L += (v == 1) ? src1[k] : (v == 2 ? src2[k] : T(0));
+      const size_t ix = (size_t)(v * ND + k) * base + e;
+      double out;
+      if (write_rhs) {
+        out = (double)L;
+      } else if (s.stage == 0) {
+        out = s.uin[ix] + dt * (double)L;
+      } else {
+        out = 0.5 * s.un[ix] + 0.5 * (s.uin[ix] + dt * (double)L);
+      }
+      bad |= !isfinite(out);
+      s.uout[ix] = out;
+      if (k == 0 && s.mean) s.mean[(size_t)v * ne + e] = out;
+    }
+  }
+  if (bad) atomicOr(s.err, ERR_NONFINITE);
+}
+
+// ------------------------------------------------------------------------ SLOPELIM + WETDRY
+__device__ __forceinline__ float minmod(float a, float b) {
+  if (a > 0.f && b > 0.f) return a < b ? a : b;
+  if (a < 0.f && b < 0.f) return a > b ? a : b;
+  return 0.f;
+}
+__device__ __forceinline__ double minmod(double a, double b) {
+  if (a > 0.0 && b > 0.0) return a < b ? a : b;
+  if (a < 0.0 && b < 0.0) return a > b ? a : b;
+  return 0.0;
+}
+
+constexpr double WD_TOL = 1e-10;  // m: depths within this of h0 count as "at h0"
+
+// Cockburn-Shu minmod limiter on the linear modes of each variable (nu = 1.5), against
+// neighbour means read from `mean` (written by the element kernel, so unaffected by this pass);
+// then the wet/dry operator (double): vertex depths of the linear part, flatten if the mean depth
+// <= h0 (dry), else lift vertices below h0 to h0 and rescale the others' excess (mean kept);
+// momentum removed where dry, or partially wet with the mean surface below the highest bed of the
+// vertices at h0; at p = 2 limited or non-wet elements drop their quadratic modes.
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_limwd(const DevMesh m, double *u, const double *mean,
+                                               uint8_t *wd, const Phys ph, int *err, int do_lim,
+                                               int do_wd) {
+  constexpr int ND = nd_of(P);
+  const int ne = m.ne;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const Tab<T> &tb = ctab<T>(P);
+  if (do_lim) {
+    const T nu = T(1.5);
+    int nb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nb[j] = m.nbr[(size_t)j * ne + e];
+    const unsigned code = m.limj[e];
+    const T *A = (const T *)m.lima;
+    bool any = false;
+#pragma unroll 1
+    for (int v = 0; v < 3; ++v) {
+      const T u0 = (T)u[(size_t)(v * ND) * ne + e];
+      const T u1 = (T)u[(size_t)(v * ND + 1) * ne + e];
+      const T u2 = (T)u[(size_t)(v * ND + 2) * ne + e];
+      T ub[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) ub[j] = nb[j] >= 0 ? (T)mean[(size_t)v * ne + nb[j]] : u0;
+      T d[3];
+      bool act = false;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T ut = u1 * tb.phm[i][1] + u2 * tb.phm[i][2];
+        const unsigned c = (code >> (4 * i)) & 15u;
+        const int j1 = c & 3, j2 = c >> 2;
+        T db = T(0);
+        if (j1 != 3) db = A[(size_t)(2 * i) * ne + e] * (ub[j1] - u0) + A[(size_t)(2 * i + 1) * ne + e] * (ub[j2] - u0);
+        d[i] = minmod(ut, nu * db);
+        act |= d[i] != ut;
+      }
+      if (!act) continue;
+      any = true;
+      T pos = 0, neg = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        pos += d[i] > T(0) ? d[i] : T(0);
+        neg += d[i] < T(0) ? -d[i] : T(0);
+      }
+      const T tp = pos > T(0) ? (neg / pos < T(1) ? neg / pos : T(1)) : T(0);
+      const T tm = neg > T(0) ? (pos / neg < T(1) ? pos / neg : T(1)) : T(0);
+      T dh[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dh[i] = tp * (d[i] > T(0) ? d[i] : T(0)) - tm * (d[i] < T(0) ? -d[i] : T(0));
+      // linear function with deviations dh at the midpoints of local edges 0 and 1
+      const T det = tb.phm[0][1] * tb.phm[1][2] - tb.phm[0][2] * tb.phm[1][1];
+      u[(size_t)(v * ND + 1) * ne + e] = (double)((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) / det);
+      u[(size_t)(v * ND + 2) * ne + e] = (double)((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) / det);
+    }
+    if constexpr (P == 2) {
+      if (any)
+        for (int v = 0; v < 3; ++v)
+          for (int k = 3; k < ND; ++k) u[(size_t)(v * ND + k) * ne + e] = 0.0;
+    }
+  }
+  if (do_wd) {  // 1: apply the operator, 2: classify only (flags from the current state)
+    const bool write = do_wd == 1;
+    const double h0 = ph.h0;
+    const double hbv[3] = {m.hbv[e], m.hbv[ne + e], m.hbv[2 * (size_t)ne + e]};
+    const double z0 = u[e], z1 = u[(size_t)ne + e], z2 = u[2 * (size_t)ne + e];
+    // zeta at the reference vertices (-1,-1), (1,-1), (-1,1): psi_10 = (-1, 1, 0), psi_01 = (-1, -1, 2)
+    double H[3] = {z0 - z1 - z2 + hbv[0], z0 + z1 - z2 + hbv[1], z0 + 2.0 * z2 + hbv[2]};
+    const double Hm = (H[0] + H[1] + H[2]) / 3.0;
+    int flag;
+    bool changed = false;
+    if (Hm <= h0 + WD_TOL) {
+      H[0] = H[1] = H[2] = Hm;
+      flag = 2;
+      changed = true;
+    } else {
+      const double hmin = fmin(H[0], fmin(H[1], H[2]));
+      if (hmin < h0) {
+        double ex = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (H[i] >= h0) ex += H[i] - h0;
+        const double S = (3.0 * Hm - 3.0 * h0) / ex;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) H[i] = (H[i] < h0) ? h0 : h0 + (H[i] - h0) * S;
+        changed = true;
+      }
+      flag = (H[0] > h0 + WD_TOL && H[1] > h0 + WD_TOL && H[2] > h0 + WD_TOL) ? 0 : 1;
+    }
+    if (changed && write) {
+      const double zv0 = H[0] - hbv[0], zv1 = H[1] - hbv[1], zv2 = H[2] - hbv[2];
+      u[(size_t)ne + e] = 0.5 * (zv1 - zv0);
+      u[2 * (size_t)ne + e] = (2.0 * zv2 - zv0 - zv1) / 6.0;
+    }
+    bool zero_q = flag == 2;
+    if (flag == 1) {
+      double bed = -INFINITY;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (H[i] <= h0 + WD_TOL && -hbv[i] > bed) bed = -hbv[i];
+      if (z0 < bed) zero_q = true;
+    }
+    if (zero_q && write)
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {
+        u[(size_t)(ND + k) * ne + e] = 0.0;
+        u[(size_t)(2 * ND + k) * ne + e] = 0.0;
+      }
+    if constexpr (P == 2) {
+      if (flag != 0 && write)
+        for (int v = 0; v < 3; ++v)
+          for (int k = 3; k < ND; ++k) u[(size_t)(v * ND + k) * ne + e] = 0.0;
+    }
+    wd[e] = (uint8_t)flag;
+    if (Hm < 0.0) atomicOr(err, ERR_NEGDEPTH);
+  }
+}
+
+// ------------------------------------------------------------------------ launchers
+// Upload the double tables and their float rounding into this translation unit's constant memory.
+static inline void upload_tables_tu(const Tab<double> td[2]) {
+  Tab<float> tf[2];
+  for (int p = 0; p < 2; ++p) {
+    const double *src = reinterpret_cast<const double *>(&td[p]);
+    float *dst = reinterpret_cast<float *>(&tf[p]);
+    for (size_t i = 0; i < sizeof(Tab<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
+  }
+  cudaMemcpyToSymbol(c_td, td, sizeof(Tab<double>) * 2);
+  cudaMemcpyToSymbol(c_tf, tf, sizeof(Tab<float>) * 2);
+}
+
+inline int nblocks(long n, int b) { return (int)((n + b - 1) / b); }
+
+template <typename T>
+void launch_forcing_t(const DevMesh &m, const Phys &ph, const Clock &clk, int stage, double tf, void *frc,
+                      const LaunchCfg &c) {
+  k_forcing<T><<<nblocks(m.nn, 256), 256, 0, c.stream>>>(m.nodexy, m.nn, ph, clk, stage, tf, (T *)frc);
+}
+
+template <typename T>
+void launch_edge_t(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, const LaunchCfg &c) {
+  if (m.nint == 0) return;
+  if (p == 1)
+    k_edge<1, T><<<nblocks(m.nint, c.block), c.block, 0, c.stream>>>(m, s, ph);
+  else
+    k_edge<2, T><<<nblocks(m.nint, c.block), c.block, 0, c.stream>>>(m, s, ph);
+}
+
+template <typename T>
+void launch_element_t(int p, bool split, bool write_rhs, const DevMesh &m, const StageArgs &s, const Phys &ph,
+                      const LaunchCfg &c) {
+  const int nb = nblocks(m.ne, c.block), wr = write_rhs ? 1 : 0;
+  if (p == 1) {
+    if (split)
+      k_element<1, T, true><<<nb, c.block, 0, c.stream>>>(m, s, ph, wr);
+    else
+      k_element<1, T, false><<<nb, c.block, 0, c.stream>>>(m, s, ph, wr);
+  } else {
+    if (split)
+      k_element<2, T, true><<<nb, c.block, 0, c.stream>>>(m, s, ph, wr);
+    else
+      k_element<2, T, false><<<nb, c.block, 0, c.stream>>>(m, s, ph, wr);
+  }
+}
+
+template <typename T>
+void launch_limwd_t(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean, uint8_t *wd,
+                    const Phys &ph, int *err, const LaunchCfg &c) {
+  const int nb = nblocks(m.ne, c.block);
+  if (p == 1)
+    k_limwd<1, T><<<nb, c.block, 0, c.stream>>>(m, u, mean, wd, ph, err, do_lim, do_wd);
+  else
+    k_limwd<2, T><<<nb, c.block, 0, c.stream>>>(m, u, mean, wd, ph, err, do_lim, do_wd);
+}
+
+}  // namespace dg

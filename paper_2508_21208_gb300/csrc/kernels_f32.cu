@@ -1,0 +1,24 @@
+// kernels_f32.cu -- stage kernels instantiated with T = float.
+#include "kernels.cuh"
+
+namespace dg {
+
+void upload_tables_f32(const Tab<double> td[2]) { upload_tables_tu(td); }
+
+void launch_forcing_f32(const DevMesh &m, const Phys &ph, const Clock &clk, int stage, double t_fixed,
+                        void *frc, const LaunchCfg &c) {
+  launch_forcing_t<float>(m, ph, clk, stage, t_fixed, frc, c);
+}
+void launch_edge_f32(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, const LaunchCfg &c) {
+  launch_edge_t<float>(p, m, s, ph, c);
+}
+void launch_element_f32(int p, bool split, bool write_rhs, const DevMesh &m, const StageArgs &s,
+                        const Phys &ph, const LaunchCfg &c) {
+  launch_element_t<float>(p, split, write_rhs, m, s, ph, c);
+}
+void launch_limwd_f32(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean,
+                      uint8_t *wd, const Phys &ph, int *err, const LaunchCfg &c) {
+  launch_limwd_t<float>(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
+}
+
+}  // namespace dg

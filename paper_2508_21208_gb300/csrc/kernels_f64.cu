@@ -1,0 +1,24 @@
+// kernels_f64.cu -- stage kernels instantiated with T = double.
+#include "kernels.cuh"
+
+namespace dg {
+
+void upload_tables_f64(const Tab<double> td[2]) { upload_tables_tu(td); }
+
+void launch_forcing_f64(const DevMesh &m, const Phys &ph, const Clock &clk, int stage, double t_fixed,
+                        void *frc, const LaunchCfg &c) {
+  launch_forcing_t<double>(m, ph, clk, stage, t_fixed, frc, c);
+}
+void launch_edge_f64(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, const LaunchCfg &c) {
+  launch_edge_t<double>(p, m, s, ph, c);
+}
+void launch_element_f64(int p, bool split, bool write_rhs, const DevMesh &m, const StageArgs &s,
+                        const Phys &ph, const LaunchCfg &c) {
+  launch_element_t<double>(p, split, write_rhs, m, s, ph, c);
+}
+void launch_limwd_f64(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean,
+                      uint8_t *wd, const Phys &ph, int *err, const LaunchCfg &c) {
+  launch_limwd_t<double>(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
+}
+
+}  // namespace dg
