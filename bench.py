@@ -144,6 +144,7 @@ def time_steps(model, steps, warmup, stream, flush, per_kernel=False):
     model.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     kt = {}
+    torch.cuda.profiler.start()  # an ncu run with --profile-from-start off sees only these steps
     for i in range(steps):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -155,6 +156,7 @@ def time_steps(model, steps, warmup, stream, flush, per_kernel=False):
             for name, ms in model.kernel_times():
                 kt.setdefault(name, []).append(ms)
     stream.synchronize()
+    torch.cuda.profiler.stop()
     model.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
     return ms, kt
@@ -248,6 +250,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile", choices=["storm", "storm-mixed", "shelf", "shelf-mixed"],
+                    help="run 3 steps of one workload with the split variant, block 64 (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -262,6 +266,14 @@ def main():
     from paper_2508_21208_gb300.build import build_library
     build_library()
     torch.cuda.set_device(local)
+    if args.profile:
+        mixed = synth.FP32_MIXED if args.profile.endswith("mixed") else synth.FP64
+        case = synth.config3(precision=mixed) if args.profile.startswith("storm") else synth.config2(precision=mixed)
+        m = make_model(case, torch.cuda.Stream(), variant=1, block=64)
+        m.step(3)
+        m.sync()
+        print(json.dumps({"profile": args.profile, "elements": case.mesh.n_elems, "steps": 3}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
