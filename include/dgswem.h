@@ -54,6 +54,7 @@ extern "C" {
 #define DGSWEM_ETIMEOUT -6   /* a bounded device-side wait gave up (ensemble grid barrier) */
 #define DGSWEM_ENOMEM -7     /* the attached workspace is smaller than dgswem_workspace_size */
 #define DGSWEM_ESTATE -8     /* call out of order (e.g. step before attach) */
+#define DGSWEM_ETOOBIG -9    /* input larger than a fixed-size library buffer allows */
 
 /* boundary edge types (Sec. 2.1: Gamma_land, Gamma_ocean) */
 #define DGSWEM_BC_LAND 0 /* no normal flow: mirror ghost state */
@@ -220,6 +221,33 @@ DGSWEM_API int dgswem_ensemble_info(dgswem_ctx *ctx, int32_t member, double *dt,
 /* Test hook: when on, one block skips every grid-barrier arrival, so the other blocks' bounded
  * waits expire and the step reports DGSWEM_ETIMEOUT instead of hanging. */
 DGSWEM_API int dgswem_ensemble_set_fault(dgswem_ctx *ctx, int32_t skip_arrival);
+
+/* ---- allocation-free mass sums ----
+ * The paper has no counterpart: this is a service for callers that may not allocate device
+ * memory.  Examples are a host model or coupler that owns the whole GPU memory budget and
+ * forbids allocations by the libraries it calls, and a time-critical loop where the implicit
+ * synchronisation and possible failure of cudaMalloc are not acceptable.  Such a caller passes
+ * only its own device arrays; the library neither allocates nor frees anything.
+ *
+ * Computes, like dgswem_mass, d_out[0] = sum_e area[e] * zeta00[e] and
+ * d_out[1] = sum_e area[e] * (zeta00[e] + hb_mean[e]) as compensated double sums in a fixed
+ * block order, from caller-owned device arrays of n_elems doubles (element mean surface, element
+ * area, element mean bathymetry); d_out is a caller-owned device array of two doubles.  Work is
+ * queued on `stream` (cudaStream_t as void*, NULL = legacy default stream); the call returns
+ * without waiting, so read d_out after synchronising that stream.
+ *
+ * The block partial sums live in one fixed device buffer inside the library, sized for at most
+ * DGSWEM_NOALLOC_MAX_ELEMS elements (1 MiB; every GPU that loads the library holds it until the
+ * process exits).  Larger n_elems is rejected with DGSWEM_ETOOBIG before any device work;
+ * n_elems < 1 or a NULL pointer gives DGSWEM_EINVAL.  The first call on each device looks up the
+ * buffer's device address (that device must be current), so make the first call before any
+ * stream capture.  All calls share the buffer: calls that can overlap on the GPU (different
+ * streams, or different host threads) race and must be serialised by the caller.  Each call
+ * overwrites every partial it reads, so no state carries over from a previous call. */
+#define DGSWEM_NOALLOC_MAX_ELEMS (1 << 26)
+DGSWEM_API int dgswem_mass_noalloc(const double *d_zeta00, const double *d_area,
+                                   const double *d_hb_mean, int32_t n_elems, double *d_out,
+                                   void *stream);
 
 #ifdef __cplusplus
 }

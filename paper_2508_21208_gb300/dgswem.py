@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libdgswem.so")
 
 DGSWEM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "EMESH", -3: "ECUDA", -4: "ENONFINITE", -5: "ENEGDEPTH", -6: "ETIMEOUT",
-          -7: "ENOMEM", -8: "ESTATE"}
+          -7: "ENOMEM", -8: "ESTATE", -9: "ETOOBIG"}
 VARIANT_AUTO, VARIANT_SPLIT, VARIANT_FUSED = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
 
@@ -86,6 +86,7 @@ SIGNATURES = [
     ("dgswem_ensemble_get_state", C.c_int, [_vp, C.c_int32, _dp, _dp, _dp]),
     ("dgswem_ensemble_info", C.c_int, [_vp, C.c_int32, _dp, _dp, C.POINTER(C.c_int64)]),
     ("dgswem_ensemble_set_fault", C.c_int, [_vp, C.c_int32]),
+    ("dgswem_mass_noalloc", C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, _vp]),
 ]
 
 
