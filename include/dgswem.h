@@ -206,10 +206,18 @@ DGSWEM_API int dgswem_graph_info(dgswem_ctx *ctx, int32_t *kernels_per_step, int
 /* ---- batched ensemble (several scenarios, meshes of uneven size) ----
  * n members; member i uses meshes[i], bathy[i], params[i] and inits[i] (inits may be NULL).
  * Members that pass the same mesh and bathymetry pointers share one copy of the static mesh
- * data.  All members must use the same p and precision.  A step advances every member by one
- * of its own time steps in one persistent cooperative kernel launch (grid barriers between the
- * phases, each wait bounded in time), captured in a CUDA graph; tuning->block picks the
- * element tile. */
+ * data.  All members must use the same p and precision; each has its own CFL time step, forcing
+ * and wet/dry state.  A step advances every member by one of its own time steps, either in one
+ * persistent cooperative kernel launch (forcing, element update and limiter/wet-dry phases over a
+ * flat list of (member, element tile) work items, separated by grid barriers whose waits are
+ * bounded in time) or in one launch per phase; the step is captured in a CUDA graph.  For an
+ * ensemble, tuning->variant selects DGSWEM_ENSEMBLE_PERSISTENT or DGSWEM_ENSEMBLE_PHASED (0:
+ * the autotuner times both), tuning->block the tile size (0: timed among 64, 128, 256).  The
+ * element update always computes its own edge fluxes (the fused organisation).  dgswem_step,
+ * dgswem_sync, dgswem_set_kernel_timing, dgswem_kernel_times, dgswem_graph_info,
+ * dgswem_workspace_size, dgswem_attach and dgswem_destroy apply to an ensemble context. */
+#define DGSWEM_ENSEMBLE_PERSISTENT 1
+#define DGSWEM_ENSEMBLE_PHASED 2
 DGSWEM_API int dgswem_ensemble_create(int32_t n, const dgswem_mesh *const *meshes,
                            const double *const *bathy, const dgswem_params *params,
                            const dgswem_init *inits, const dgswem_tuning *tuning,

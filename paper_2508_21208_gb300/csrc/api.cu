@@ -13,21 +13,7 @@
 using namespace dg;
 
 namespace {
-
 constexpr size_t kAlign = 256;
-
-struct Carver {
-  char *base;
-  size_t off = 0;
-  template <class X>
-  X *take(size_t count) {
-    off = (off + kAlign - 1) / kAlign * kAlign;
-    X *p = base ? reinterpret_cast<X *>(base + off) : nullptr;
-    off += std::max<size_t>(count, 1) * sizeof(X);
-    return p;
-  }
-};
-
 }  // namespace
 
 // ------------------------------------------------------------------ helpers shared with ensemble.cu
@@ -117,12 +103,10 @@ static std::vector<char> typed(const std::vector<double> &v, bool mixed) {
 }
 
 // ------------------------------------------------------------------ workspace layout
-static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
-  const HostMesh &H = c->hm;
-  const int ne = H.ne, nn = H.nn, nint = H.nint, ND = c->ND, NQE = nqe_of(c->P);
-  const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
-  Carver k{base};
-  DevMesh &m = c->dm;
+void carve_mesh(Carver &k, const HostMesh &H, int p, bool mixed, DevMesh &m, int **perm, int **iperm) {
+  const int ne = H.ne, nn = H.nn, nint = H.nint;
+  (void)p;
+  const size_t tsz = mixed ? sizeof(float) : sizeof(double);
   m.ne = ne;
   m.nn = nn;
   m.nint = nint;
@@ -141,8 +125,16 @@ static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
   m.edgeo = k.take<char>(tsz * 3 * nint);
   m.edhb = k.take<double>(2 * (size_t)nint);
   m.nodexy = k.take<double>(2 * (size_t)nn);
-  c->d_perm = k.take<int>(ne);
-  c->d_iperm = k.take<int>(ne);
+  *perm = k.take<int>(ne);
+  *iperm = k.take<int>(ne);
+}
+
+static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
+  const HostMesh &H = c->hm;
+  const int ne = H.ne, nn = H.nn, nint = H.nint, ND = c->ND, NQE = nqe_of(c->P);
+  const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
+  Carver k{base};
+  carve_mesh(k, H, c->P, c->mixed, c->dm, &c->d_perm, &c->d_iperm);
   const size_t nu = 3 * (size_t)ND * ne;
   c->U0 = k.take<double>(nu);
   c->U1 = k.take<double>(nu);
@@ -293,6 +285,37 @@ int attach_common(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream) 
   return ctx_cuda(c, cudaGetLastError(), "table upload");
 }
 
+int upload_mesh(dgswem_ctx *c, const HostMesh &H, const DevMesh &m, int *perm, int *iperm) {
+  cudaStream_t s = c->st;
+  auto put = [&](const void *dst, const void *src, size_t n) -> int {
+    if (n == 0) return 0;
+    return ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(dst), src, n, cudaMemcpyHostToDevice, s), "upload");
+  };
+  const size_t base = c->host_keep.size();
+  c->host_keep.push_back(typed(H.geo, c->mixed));
+  c->host_keep.push_back(typed(H.lima, c->mixed));
+  c->host_keep.push_back(typed(H.edgeo, c->mixed));
+  int r = 0;
+  r |= put(m.geo, c->host_keep[base].data(), c->host_keep[base].size());
+  r |= put(m.hbv, H.hbv.data(), H.hbv.size() * sizeof(double));
+  r |= put(m.area, H.area.data(), H.area.size() * sizeof(double));
+  r |= put(m.inradius, H.inradius.data(), H.inradius.size() * sizeof(double));
+  r |= put(m.nbr, H.nbr.data(), H.nbr.size() * sizeof(int));
+  r |= put(m.nle, H.nle.data(), H.nle.size());
+  r |= put(m.vnode, H.vnode.data(), H.vnode.size() * sizeof(int));
+  r |= put(m.lima, c->host_keep[base + 1].data(), c->host_keep[base + 1].size());
+  r |= put(m.limj, H.limj.data(), H.limj.size() * sizeof(uint16_t));
+  r |= put(m.eledge, H.eledge.data(), H.eledge.size() * sizeof(int));
+  r |= put(m.edel, H.edel.data(), H.edel.size() * sizeof(int));
+  r |= put(m.edle, H.edle.data(), H.edle.size());
+  r |= put(m.edgeo, c->host_keep[base + 2].data(), c->host_keep[base + 2].size());
+  r |= put(m.edhb, H.edhb.data(), H.edhb.size() * sizeof(double));
+  r |= put(m.nodexy, H.nodexy.data(), H.nodexy.size() * sizeof(double));
+  r |= put(perm, H.perm.data(), H.perm.size() * sizeof(int));
+  r |= put(iperm, H.iperm.data(), H.iperm.size() * sizeof(int));
+  return r ? c->sticky : 0;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -351,36 +374,8 @@ int dgswem_workspace_size(const dgswem_ctx *ctx, size_t *bytes) {
 }
 
 static int upload_static(dgswem_ctx *c) {
-  const HostMesh &H = c->hm;
-  cudaStream_t s = c->st;
-  const DevMesh &m = c->dm;
   c->host_keep.clear();
-  auto put = [&](const void *dst, const void *src, size_t n) -> int {
-    if (n == 0) return 0;
-    return ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(dst), src, n, cudaMemcpyHostToDevice, s), "upload");
-  };
-  c->host_keep.push_back(typed(H.geo, c->mixed));
-  c->host_keep.push_back(typed(H.lima, c->mixed));
-  c->host_keep.push_back(typed(H.edgeo, c->mixed));
-  int r = 0;
-  r |= put(m.geo, c->host_keep[0].data(), c->host_keep[0].size());
-  r |= put(m.hbv, H.hbv.data(), H.hbv.size() * sizeof(double));
-  r |= put(m.area, H.area.data(), H.area.size() * sizeof(double));
-  r |= put(m.inradius, H.inradius.data(), H.inradius.size() * sizeof(double));
-  r |= put(m.nbr, H.nbr.data(), H.nbr.size() * sizeof(int));
-  r |= put(m.nle, H.nle.data(), H.nle.size());
-  r |= put(m.vnode, H.vnode.data(), H.vnode.size() * sizeof(int));
-  r |= put(m.lima, c->host_keep[1].data(), c->host_keep[1].size());
-  r |= put(m.limj, H.limj.data(), H.limj.size() * sizeof(uint16_t));
-  r |= put(m.eledge, H.eledge.data(), H.eledge.size() * sizeof(int));
-  r |= put(m.edel, H.edel.data(), H.edel.size() * sizeof(int));
-  r |= put(m.edle, H.edle.data(), H.edle.size());
-  r |= put(m.edgeo, c->host_keep[2].data(), c->host_keep[2].size());
-  r |= put(m.edhb, H.edhb.data(), H.edhb.size() * sizeof(double));
-  r |= put(m.nodexy, H.nodexy.data(), H.nodexy.size() * sizeof(double));
-  r |= put(c->d_perm, H.perm.data(), H.perm.size() * sizeof(int));
-  r |= put(c->d_iperm, H.iperm.data(), H.iperm.size() * sizeof(int));
-  return r ? c->sticky : 0;
+  return upload_mesh(c, c->hm, c->dm, c->d_perm, c->d_iperm);
 }
 
 static int autotune(dgswem_ctx *c, int *best_variant, int *best_block) {

@@ -14,6 +14,19 @@ struct TuneEntry {
 
 struct EnsembleState;  // ensemble.cu
 
+// Carves aligned sub-buffers out of one workspace (or only measures, when base is null).
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <class X>
+  X *take(size_t count) {
+    off = (off + 255) / 256 * 256;
+    X *p = base ? reinterpret_cast<X *>(base + off) : nullptr;
+    off += (count > 0 ? count : 1) * sizeof(X);
+    return p;
+  }
+};
+
 struct dgswem_ctx {
   bool ensemble = false;
   dgswem_params prm{};
@@ -67,6 +80,9 @@ void upload_all_tables();
 int read_error_word(dgswem_ctx *c);
 int attach_common(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream);
 int capture_graph(dgswem_ctx *c, int variant, int block, bool timing);
+void carve_mesh(Carver &k, const dg::HostMesh &H, int p, bool mixed, dg::DevMesh &m, int **perm,
+                int **iperm);
+int upload_mesh(dgswem_ctx *c, const dg::HostMesh &H, const dg::DevMesh &m, int *perm, int *iperm);
 // ensemble.cu
 int ensemble_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream);
 void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names);

@@ -104,6 +104,30 @@ struct StageArgs {
   double tide_t;           // stage time when clk.step is null (single operator calls)
 };
 
+// One ensemble member (scenario) as the ensemble kernels see it.
+struct MemberDev {
+  DevMesh m;               // the member's mesh statics (shared with members on the same mesh)
+  Phys ph;
+  double *U0, *U1, *mean;  // its own state
+  uint8_t *wd;
+  void *frc;               // T [3][nn]
+  double t0, dt;           // stage time = t0 + (step + stage) * dt (its own dt)
+  int etile0, ntile0;      // first element / node tile of this member in the flat tile lists
+};
+
+struct EnsArgs {
+  const MemberDev *mem;
+  const int *etile;        // element tile -> member
+  const int *ntile;        // node tile -> member (members with a hurricane)
+  int n_etile, n_ntile;
+  long long *step;         // shared step counter
+  unsigned *bar;           // grid barrier: [0] arrivals, [1] generation
+  int *err;
+  int fault;               // test hook: the last block never arrives at a barrier
+  int any_limwd;
+  unsigned long long timeout_ns;
+};
+
 // error word bits
 constexpr int ERR_NONFINITE = 1;
 constexpr int ERR_NEGDEPTH = 2;
@@ -143,7 +167,10 @@ struct LaunchCfg {
                             const StageArgs &s, const Phys &ph, const LaunchCfg &c);             \
   void launch_limwd_##SUF(int p, bool do_lim, int do_wd, const DevMesh &m, double *u,            \
                           const double *mean, uint8_t *wd, const Phys &ph, int *err,             \
-                          const LaunchCfg &c);
+                          const LaunchCfg &c);                                                   \
+  cudaError_t launch_ensemble_##SUF(int p, bool persistent, const EnsArgs &a, int block, int grid, \
+                                    cudaStream_t s);                                             \
+  int ensemble_blocks_per_sm_##SUF(int p, int block);
 DG_DECLARE_LAUNCHERS(f64)
 DG_DECLARE_LAUNCHERS(f32)
 #undef DG_DECLARE_LAUNCHERS
@@ -167,6 +194,14 @@ inline void launch_limwd(bool mixed, int p, bool do_lim, int do_wd, const DevMes
                          const LaunchCfg &c) {
   mixed ? launch_limwd_f32(p, do_lim, do_wd, m, u, mean, wd, ph, err, c)
         : launch_limwd_f64(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
+}
+inline cudaError_t launch_ensemble(bool mixed, int p, bool persistent, const EnsArgs &a, int block, int grid,
+                                   cudaStream_t s) {
+  return mixed ? launch_ensemble_f32(p, persistent, a, block, grid, s)
+               : launch_ensemble_f64(p, persistent, a, block, grid, s);
+}
+inline int ensemble_blocks_per_sm(bool mixed, int p, int block) {
+  return mixed ? ensemble_blocks_per_sm_f32(p, block) : ensemble_blocks_per_sm_f64(p, block);
 }
 void upload_common_tables(const Tab<double> td[2]);
 

@@ -113,11 +113,8 @@ __device__ __forceinline__ void load_modes(const double *u, int ne, int e, T w[3
 // C_d = min(0.75 + 0.067 |U|, 3.5) 1e-3.  Output per node: tau/rho_w (x, y) and the pressure
 // anomaly (p - pn)/rho_w (only its gradient enters the momentum source).
 template <typename T>
-__global__ void k_forcing(const double *nodexy, int nn, Phys ph, Clock clk, int stage, double t_fixed,
-                          T *frc) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nn) return;
-  const double t = stage_time(clk, stage, t_fixed);
+__device__ __forceinline__ void forcing_body(const double *nodexy, int nn, const Phys &ph, double t, T *frc,
+                                             int n) {
   const double ch = cos(ph.heading), sh = sin(ph.heading);
   const T dx = (T)(nodexy[n] - (ph.x0 + ph.vt * ch * t));
   const T dy = (T)(nodexy[nn + n] - (ph.y0 + ph.vt * sh * t));
@@ -144,6 +141,23 @@ __global__ void k_forcing(const double *nodexy, int nn, Phys ph, Clock clk, int 
   frc[n] = k * ux;
   frc[nn + n] = k * uy;
   frc[2 * nn + n] = pa / (T)ph.rho_w;
+}
+
+template <typename T>
+__global__ void k_forcing(const double *nodexy, int nn, Phys ph, Clock clk, int stage, double t_fixed,
+                          T *frc) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  forcing_body<T>(nodexy, nn, ph, stage_time(clk, stage, t_fixed), frc, n);
+}
+
+// Copy the edge basis table of degree P into shared memory (indexed by thread-varying local edges).
+template <int P, typename T>
+__device__ __forceinline__ void load_phe(T (*s_phe)[nqe_of(P)][nd_of(P)]) {
+  constexpr int ND = nd_of(P), NQE = nqe_of(P);
+  const Tab<T> &tb = ctab<T>(P);
+  for (int i = threadIdx.x; i < 3 * NQE * ND; i += blockDim.x)
+    s_phe[i / (NQE * ND)][(i / ND) % NQE][i % ND] = tb.phe[i / (NQE * ND)][(i / ND) % NQE][i % ND];
 }
 
 // ------------------------------------------------------------------------ EDGE (split variant)
@@ -207,17 +221,12 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
 // pressure gradient -H dp_a/dx with linear p_a) are integrated in closed form through the basis
 // orthogonality; the area rule is exact for them, so this is the same discrete operator.
 template <int P, typename T, bool SPLIT>
-__global__ void __launch_bounds__(256)
-    k_element(const DevMesh m, const StageArgs s, const Phys ph, const int write_rhs) {
+__device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &s, const Phys &ph,
+                                             const int write_rhs, const int e,
+                                             const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
   constexpr int ND = nd_of(P), NQA = nqa_of(P), NQE = nqe_of(P);
-  __shared__ T s_phe[3][NQE][ND];
   const Tab<T> &tb = ctab<T>(P);
-  for (int i = threadIdx.x; i < 3 * NQE * ND; i += blockDim.x)
-    s_phe[i / (NQE * ND)][(i / ND) % NQE][i % ND] = tb.phe[i / (NQE * ND)][(i / ND) % NQE][i % ND];
-  __syncthreads();
   const int ne = m.ne;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
   const double ts = stage_time(s.clk, s.stage, s.tide_t);
   const T g = (T)ph.g;
   T w[3][ND];
@@ -463,6 +472,17 @@ __global__ void __launch_bounds__(256)
   if (bad) atomicOr(s.err, ERR_NONFINITE);
 }
 
+template <int P, typename T, bool SPLIT>
+__global__ void __launch_bounds__(256)
+    k_element(const DevMesh m, const StageArgs s, const Phys ph, const int write_rhs) {
+  __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
+  load_phe<P, T>(s_phe);
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  element_body<P, T, SPLIT>(m, s, ph, write_rhs, e, s_phe);
+}
+
 // ------------------------------------------------------------------------ SLOPELIM + WETDRY
 __device__ __forceinline__ float minmod(float a, float b) {
   if (a > 0.f && b > 0.f) return a < b ? a : b;
@@ -484,13 +504,10 @@ constexpr double WD_TOL = 1e-10;  // m: depths within this of h0 count as "at h0
 // momentum removed where dry, or partially wet with the mean surface below the highest bed of the
 // vertices at h0; at p = 2 limited or non-wet elements drop their quadratic modes.
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_limwd(const DevMesh m, double *u, const double *mean,
-                                               uint8_t *wd, const Phys ph, int *err, int do_lim,
-                                               int do_wd) {
+__device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const double *mean, uint8_t *wd,
+                                           const Phys &ph, int *err, int do_lim, int do_wd, const int e) {
   constexpr int ND = nd_of(P);
   const int ne = m.ne;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
   const Tab<T> &tb = ctab<T>(P);
   if (do_lim) {
     const T nu = T(1.5);
@@ -599,6 +616,187 @@ __global__ void __launch_bounds__(256) k_limwd(const DevMesh m, double *u, const
     wd[e] = (uint8_t)flag;
     if (Hm < 0.0) atomicOr(err, ERR_NEGDEPTH);
   }
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_limwd(const DevMesh m, double *u, const double *mean,
+                                               uint8_t *wd, const Phys ph, int *err, int do_lim,
+                                               int do_wd) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  limwd_body<P, T>(m, u, mean, wd, ph, err, do_lim, do_wd, e);
+}
+
+// ------------------------------------------------------------------------ ensemble
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch.  Thread 0 of each block arrives on a counter; the
+// last arrival resets it and bumps the generation that the others wait on.  Every wait is bounded
+// by a.timeout_ns: on expiry the block records ERR_TIMEOUT and the kernel returns instead of
+// hanging.  `skip` (test hook) makes this block not arrive.  Returns false once a timeout is seen.
+__device__ __forceinline__ bool grid_barrier(const EnsArgs &a, bool skip) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = a.bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    bool last = false;
+    if (!skip) {
+      const unsigned arrived = atomicAdd(a.bar, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(a.bar, 0u);
+        __threadfence();
+        atomicAdd(a.bar + 1, 1u);
+        last = true;
+      }
+    }
+    if (!last) {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g0) {
+        if (global_ns() - t0 > a.timeout_ns) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return (*(volatile int *)a.err & ERR_TIMEOUT) == 0;
+}
+
+// Stage arguments of member md (fused element variant: no edge scratch).
+__device__ __forceinline__ StageArgs member_stage(const MemberDev &md, const EnsArgs &a, int stage) {
+  StageArgs sa;
+  sa.uin = stage ? md.U1 : md.U0;
+  sa.un = md.U0;
+  sa.uout = stage ? md.U0 : md.U1;
+  sa.mean = md.ph.limiter ? md.mean : nullptr;
+  sa.wd = md.ph.wetdry ? md.wd : nullptr;
+  sa.eflux = nullptr;
+  sa.emode = nullptr;
+  sa.frc = md.ph.hurricane ? md.frc : nullptr;
+  sa.clk = Clock{a.step, md.t0, md.dt};
+  sa.stage = stage;
+  sa.err = a.err;
+  sa.tide_t = 0.0;
+  return sa;
+}
+
+// Copy a member descriptor into shared memory (all threads of the block work on one tile).
+__device__ __forceinline__ void load_member(MemberDev *dst, const MemberDev *src) {
+  __syncthreads();
+  const int *s = reinterpret_cast<const int *>(src);
+  int *d = reinterpret_cast<int *>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(MemberDev) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage, int t_begin, int t_step,
+                                          MemberDev *sd, const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
+  if (phase == 0) {  // WIND at the nodes of members with a hurricane
+    for (int t = t_begin; t < a.n_ntile; t += t_step) {
+      load_member(sd, &a.mem[a.ntile[t]]);
+      const int n = (t - sd->ntile0) * blockDim.x + threadIdx.x;
+      if (n < sd->m.nn)
+        forcing_body<T>(sd->m.nodexy, sd->m.nn, sd->ph, stage_time(Clock{a.step, sd->t0, sd->dt}, stage, 0.0),
+                        (T *)sd->frc, n);
+    }
+  } else {
+    for (int t = t_begin; t < a.n_etile; t += t_step) {
+      load_member(sd, &a.mem[a.etile[t]]);
+      const int e = (t - sd->etile0) * blockDim.x + threadIdx.x;
+      if (e >= sd->m.ne) continue;
+      if (phase == 1) {
+        const StageArgs sa = member_stage(*sd, a, stage);
+        element_body<P, T, false>(sd->m, sa, sd->ph, 0, e, s_phe);
+      } else if (sd->ph.limiter || sd->ph.wetdry) {
+        limwd_body<P, T>(sd->m, stage ? sd->U0 : sd->U1, sd->mean, sd->wd, sd->ph, a.err, sd->ph.limiter,
+                         sd->ph.wetdry, e);
+      }
+    }
+  }
+}
+
+// One time step of every member in one cooperative launch: per stage, WIND -> element update ->
+// limiter/wet-dry over the flat tile lists, separated by bounded grid barriers.
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_ens_persistent(const EnsArgs a) {
+  __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
+  __shared__ MemberDev sd;
+  load_phe<P, T>(s_phe);
+  __syncthreads();
+  if (*(volatile int *)a.err & ERR_TIMEOUT) return;  // an earlier step already failed
+  const bool skip = a.fault && blockIdx.x == gridDim.x - 1;
+  for (int stage = 0; stage < 2; ++stage) {
+    if (a.n_ntile > 0) {
+      ens_phase<P, T>(a, 0, stage, blockIdx.x, gridDim.x, &sd, s_phe);
+      if (!grid_barrier(a, skip)) return;
+    }
+    ens_phase<P, T>(a, 1, stage, blockIdx.x, gridDim.x, &sd, s_phe);
+    if (!grid_barrier(a, skip)) return;
+    if (a.any_limwd) {
+      ens_phase<P, T>(a, 2, stage, blockIdx.x, gridDim.x, &sd, s_phe);
+      if (stage == 0 && !grid_barrier(a, skip)) return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.step += 1;
+}
+
+// The same phases as separate launches (one tile per block); the stream orders them.
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_ens_phase(const EnsArgs a, int phase, int stage) {
+  __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
+  __shared__ MemberDev sd;
+  load_phe<P, T>(s_phe);
+  __syncthreads();
+  ens_phase<P, T>(a, phase, stage, blockIdx.x, gridDim.x, &sd, s_phe);
+}
+
+template <typename T>
+cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int block, int grid, cudaStream_t s) {
+  if (persistent) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return p == 1 ? cudaLaunchKernelEx(&cfg, k_ens_persistent<1, T>, a)
+                  : cudaLaunchKernelEx(&cfg, k_ens_persistent<2, T>, a);
+  }
+  for (int stage = 0; stage < 2; ++stage) {
+    if (a.n_ntile > 0) {
+      if (p == 1) k_ens_phase<1, T><<<a.n_ntile, block, 0, s>>>(a, 0, stage);
+      else k_ens_phase<2, T><<<a.n_ntile, block, 0, s>>>(a, 0, stage);
+    }
+    if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, 0, s>>>(a, 1, stage);
+    else k_ens_phase<2, T><<<a.n_etile, block, 0, s>>>(a, 1, stage);
+    if (a.any_limwd) {
+      if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, 0, s>>>(a, 2, stage);
+      else k_ens_phase<2, T><<<a.n_etile, block, 0, s>>>(a, 2, stage);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+int ensemble_blocks_per_sm_t(int p, int block) {
+  int n = 0;
+  if (p == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<1, T>, block, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<2, T>, block, 0);
+  return n;
 }
 
 // ------------------------------------------------------------------------ launchers

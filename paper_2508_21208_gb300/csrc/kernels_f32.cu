@@ -21,4 +21,9 @@ void launch_limwd_f32(int p, bool do_lim, int do_wd, const DevMesh &m, double *u
   launch_limwd_t<float>(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
 }
 
+cudaError_t launch_ensemble_f32(int p, bool persistent, const EnsArgs &a, int block, int grid, cudaStream_t s) {
+  return launch_ensemble_t<float>(p, persistent, a, block, grid, s);
+}
+int ensemble_blocks_per_sm_f32(int p, int block) { return ensemble_blocks_per_sm_t<float>(p, block); }
+
 }  // namespace dg

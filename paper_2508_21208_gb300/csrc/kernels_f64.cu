@@ -21,4 +21,9 @@ void launch_limwd_f64(int p, bool do_lim, int do_wd, const DevMesh &m, double *u
   launch_limwd_t<double>(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
 }
 
+cudaError_t launch_ensemble_f64(int p, bool persistent, const EnsArgs &a, int block, int grid, cudaStream_t s) {
+  return launch_ensemble_t<double>(p, persistent, a, block, grid, s);
+}
+int ensemble_blocks_per_sm_f64(int p, int block) { return ensemble_blocks_per_sm_t<double>(p, block); }
+
 }  // namespace dg

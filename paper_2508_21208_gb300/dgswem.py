@@ -18,6 +18,7 @@ DGSWEM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "EMESH", -3: "ECUDA", -4: "ENONFINITE", -5: "ENEGDEPTH", -6: "ETIMEOUT",
           -7: "ENOMEM", -8: "ESTATE", -9: "ETOOBIG"}
 VARIANT_AUTO, VARIANT_SPLIT, VARIANT_FUSED = 0, 1, 2
+ENSEMBLE_PERSISTENT, ENSEMBLE_PHASED = 1, 2
 FP64, FP32_MIXED = 0, 1
 
 
@@ -271,7 +272,7 @@ class Model(_Handle):
 class Ensemble(_Handle):
     """A batch of scenarios advanced together (dgswem_ensemble_create + dgswem_attach)."""
 
-    def __init__(self, meshes, bathys, members, block=0, stream=None):
+    def __init__(self, meshes, bathys, members, block=0, mode=0, stream=None):
         """members: list of (mesh_index, params dict, init_nodal or None)."""
         super().__init__()
         marr = [_MeshArrays(m) for m in meshes]
@@ -289,7 +290,7 @@ class Ensemble(_Handle):
             nod = None if init is None else np.ascontiguousarray(init, np.float64)
             self._keep.append(nod)
             inits[i] = Init(None, _ptr(nod), 0.0)
-        tun = Tuning(0, int(block), 0, 0)
+        tun = Tuning(int(mode), int(block), 0, 0)
         rc = self.lib.dgswem_ensemble_create(n, mesh_ptrs, hb_ptrs, prms, inits, C.byref(tun), C.byref(self.h))
         if rc != DGSWEM_OK:
             raise DgswemError(rc, "dgswem_ensemble_create")

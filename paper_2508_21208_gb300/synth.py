@@ -259,6 +259,6 @@ def ensemble(members_per_mesh: int = 16, mesh_n=ENSEMBLE_MESH_N, precision: int 
             prm = default_params(precision=precision, friction=FRICTION_QUADRATIC, cf=0.0025,
                                  limiter=1, h0=0.01, coriolis=1, coriolis_lat_deg=28.0,
                                  hurricane=1, rmax_m=40e3, vt_ms=5.0, **trk)
-            members.append((mi, prm, np.zeros((3, m.n_nodes))))
+            members.append((mi, prm, None))  # the storms start from rest (zeta = q = 0)
             sid += 1
     return meshes, bathys, members
