@@ -55,6 +55,7 @@ int check_params(const dgswem_params *p, std::string &msg) {
 Phys make_phys(const dgswem_params &p) {
   Phys ph{};
   ph.g = p.g;
+  ph.sqrt_g = std::sqrt(p.g);
   ph.h0 = p.h0;
   ph.cf = p.cf;
   ph.gn2 = p.g * p.manning_n * p.manning_n;

@@ -59,7 +59,7 @@ int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, Hos
 
 // ------------------------------------------------------------------ device-side views
 struct Phys {
-  double g, h0, cf, gn2, fcor;
+  double g, sqrt_g, h0, cf, gn2, fcor;
   double tide_amp, tide_omega, tide_phase;
   double pc, pn, rmax, hB, vt, x0, y0, heading, flat, rho_air, rho_w;
   int friction, wetdry, limiter, hurricane;

@@ -24,6 +24,44 @@ __device__ __forceinline__ double stage_time(const Clock &c, int stage, double f
   return c.step ? c.t0 + (double)(*c.step + stage) * c.dt : fixed;
 }
 
+// ------------------------------------------------------------------------ conversions
+// GB300 runs double <-> float conversions on its FP64 pipe (2 results/clock/SM).  The mixed form
+// converts every state value it reads, so these are done with integer operations instead.
+// Round-to-nearest-even double -> float for results in float's normal range (same value as the
+// hardware conversion there); smaller magnitudes give a signed zero, larger ones infinity.
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // float-biased exponent
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  unsigned r = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rb = (lo >> 28) & 1u, sticky = (lo & 0x0fffffffu) != 0u;
+  r += rb & (sticky | (r & 1u));
+  return __uint_as_float(r);
+}
+// Exact float -> double (zero and subnormals give a signed zero; infinity/NaN stay non-finite).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu, sign = u & 0x80000000u;
+  if (e == 0) return __hiloint2double((int)sign, 0);
+  const unsigned hi = sign | ((e == 255u ? 2047u : e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 0x7u) << 29));
+}
+template <typename T>
+__device__ __forceinline__ T from_d(double x) { return (T)x; }
+template <>
+__device__ __forceinline__ float from_d<float>(double x) { return d2f(x); }
+template <typename T>
+__device__ __forceinline__ double to_d(T x) { return (double)x; }
+template <>
+__device__ __forceinline__ double to_d<float>(float x) { return f2d(x); }
+// finiteness from the exponent bits (no floating-point compare)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
+}
+
 // ------------------------------------------------------------------------ point physics
 // Normal flux F(w).n of Eq. SWE with the pressure term (g/2)(H^2 - h_b^2) = (g/2) zeta (zeta + 2 h_b).
 template <typename T>
@@ -32,25 +70,36 @@ struct Side {
   T s;     // |u.n| + sqrt(g H)
 };
 
+// 1/H and sqrt(g H) come from one reciprocal square root (a divide and a square root cost about
+// ten FP64-pipe instructions each on GB300); H <= 0 falls back to a plain divide.
 template <typename T>
-__device__ __forceinline__ Side<T> side_flux(T g, const T w[3], T hb, T nx, T ny) {
+__device__ __forceinline__ Side<T> side_flux(T g, T sqrt_g, const T w[3], T hb, T nx, T ny) {
   Side<T> r;
   const T H = w[0] + hb;
   const T qn = w[1] * nx + w[2] * ny;
-  const T un = qn / H;
+  T iH, c;
+  if (H > T(0)) {
+    const T rs = rsqrt(H);
+    iH = rs * rs;
+    c = sqrt_g * H * rs;
+  } else {
+    iH = T(1) / H;
+    c = T(0);
+  }
+  const T un = qn * iH;
   const T P = T(0.5) * g * w[0] * (w[0] + T(2) * hb);
   r.F[0] = qn;
   r.F[1] = w[1] * un + P * nx;
   r.F[2] = w[2] * un + P * ny;
-  r.s = fabs(un) + sqrt(g * (H > T(0) ? H : T(0)));
+  r.s = fabs(un) + c;
   return r;
 }
 
 // Local Lax-Friedrichs flux (the numerical flux of Eq. elem_weak_form), n from wi to wo.
 template <typename T>
-__device__ __forceinline__ void llf(T g, const T wi[3], const T wo[3], T hb, T nx, T ny, T out[3]) {
-  const Side<T> a = side_flux(g, wi, hb, nx, ny);
-  const Side<T> b = side_flux(g, wo, hb, nx, ny);
+__device__ __forceinline__ void llf(T g, T sqrt_g, const T wi[3], const T wo[3], T hb, T nx, T ny, T out[3]) {
+  const Side<T> a = side_flux(g, sqrt_g, wi, hb, nx, ny);
+  const Side<T> b = side_flux(g, sqrt_g, wo, hb, nx, ny);
   const T lam = a.s > b.s ? a.s : b.s;
 #pragma unroll
   for (int v = 0; v < 3; ++v) out[v] = T(0.5) * (a.F[v] + b.F[v]) - T(0.5) * lam * (wo[v] - wi[v]);
@@ -58,10 +107,10 @@ __device__ __forceinline__ void llf(T g, const T wi[3], const T wo[3], T hb, T n
 
 // Land (no normal flow): mirror ghost zeta- = zeta+, q- = q+ - 2 (q+.n) n, then LLF.
 template <typename T>
-__device__ __forceinline__ void wall(T g, const T wi[3], T hb, T nx, T ny, T out[3]) {
+__device__ __forceinline__ void wall(T g, T sqrt_g, const T wi[3], T hb, T nx, T ny, T out[3]) {
   const T qn = wi[1] * nx + wi[2] * ny;
   const T wo[3] = {wi[0], wi[1] - T(2) * qn * nx, wi[2] - T(2) * qn * ny};
-  llf(g, wi, wo, hb, nx, ny, out);
+  llf(g, sqrt_g, wi, wo, hb, nx, ny, out);
 }
 
 template <typename T>
@@ -103,7 +152,7 @@ __device__ __forceinline__ void load_modes(const double *u, int ne, int e, T w[3
 #pragma unroll
   for (int v = 0; v < 3; ++v)
 #pragma unroll
-    for (int k = 0; k < nd_of(P); ++k) w[v][k] = (T)__ldg(&u[(size_t)(v * nd_of(P) + k) * ne + e]);
+    for (int k = 0; k < nd_of(P); ++k) w[v][k] = from_d<T>(__ldg(&u[(size_t)(v * nd_of(P) + k) * ne + e]));
 }
 
 // ------------------------------------------------------------------------ WIND
@@ -187,7 +236,7 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
   T wp[3][ND], wm[3][ND];
   load_modes<P, T>(s.uin, ne, ep, wp);
   load_modes<P, T>(s.uin, ne, em, wm);
-  const T g = (T)ph.g;
+  const T g = (T)ph.g, sqg = (T)ph.sqrt_g;
   T *F = (T *)s.eflux;
 #pragma unroll
   for (int q = 0; q < NQE; ++q) {
@@ -203,9 +252,9 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
       a[v] = x;
       b[v] = y;
     }
-    const T hb = T(0.5) * ((T(1) - tb.se[q]) * (T)hbA + (T(1) + tb.se[q]) * (T)hbB);
+    const T hb = T(0.5) * ((T(1) - tb.se[q]) * from_d<T>(hbA) + (T(1) + tb.se[q]) * from_d<T>(hbB));
     T f[3];
-    llf(g, a, b, hb, nx, ny, f);
+    llf(g, sqg, a, b, hb, nx, ny, f);
     const T wgt = hl * tb.we[q];
 #pragma unroll
     for (int v = 0; v < 3; ++v) F[(size_t)(v * NQE + q) * nint + d] = wgt * f[v];
@@ -227,8 +276,7 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
   constexpr int ND = nd_of(P), NQA = nqa_of(P), NQE = nqe_of(P);
   const Tab<T> &tb = ctab<T>(P);
   const int ne = m.ne;
-  const double ts = stage_time(s.clk, s.stage, s.tide_t);
-  const T g = (T)ph.g;
+  const T g = (T)ph.g, sqg = (T)ph.sqrt_g;
   T w[3][ND];
   load_modes<P, T>(s.uin, ne, e, w);
   const T *geo = (const T *)m.geo;
@@ -236,7 +284,7 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
   const T sx = geo[GEO_SX * (size_t)ne + e], sy = geo[GEO_SY * (size_t)ne + e];
   const T dJ = geo[GEO_DETJ * (size_t)ne + e];
   const double hbd[3] = {m.hbv[e], m.hbv[ne + e], m.hbv[2 * (size_t)ne + e]};
-  const T hb[3] = {(T)hbd[0], (T)hbd[1], (T)hbd[2]};
+  const T hb[3] = {from_d<T>(hbd[0]), from_d<T>(hbd[1]), from_d<T>(hbd[2])};
   T r[3][ND];
 #pragma unroll
   for (int v = 0; v < 3; ++v)
@@ -313,36 +361,16 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
 #pragma unroll 1
   for (int l = 0; l < 3; ++l) {
     const int j = m.nbr[(size_t)l * ne + e];
-    const T nx = geo[(GEO_NX0 + l) * (size_t)ne + e], ny = geo[(GEO_NY0 + l) * (size_t)ne + e];
     const T hl = geo[(GEO_HL0 + l) * (size_t)ne + e];
-    // end-node bathymetry of local edge l (vertex (l+1)%3 -> (l+2)%3), selected without
-    // dynamic register indexing
-    const T hbA = l == 0 ? hb[1] : (l == 1 ? hb[2] : hb[0]);
-    const T hbB = l == 0 ? hb[2] : (l == 1 ? hb[0] : hb[1]);
-    const double hbAd = l == 0 ? hbd[1] : (l == 1 ? hbd[2] : hbd[0]);
-    const double hbBd = l == 0 ? hbd[2] : (l == 1 ? hbd[0] : hbd[1]);
-    T wp[NQE][3], hbq[NQE], Fh[NQE][3];
-#pragma unroll
-    for (int q = 0; q < NQE; ++q) {
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        T x = 0;
-#pragma unroll
-        for (int k = 0; k < ND; ++k) x += w[v][k] * s_phe[l][q][k];
-        wp[q][v] = x;
-      }
-      hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hbA + (T(1) + tb.se[q]) * hbB);
-    }
-    bool weighted = false;  // Fh already carries hl * w_q
-    if (j >= 0) {
-      bool flows;
-      if constexpr (SPLIT) {
+    T Fh[NQE][3];
+    bool weighted = false;  // Fh already carries hl * w_q (flux read from the edge kernel)
+    bool have = false;      // Fh filled
+    if constexpr (SPLIT) {
+      if (j >= 0) {
         const int ed = m.eledge[(size_t)l * ne + e];
         const bool minus = ed < 0;
         const int id = ed & 0x7fffffff;
-        flows = s.emode[id] != 0;
-        if (flows) {
-          weighted = true;
+        if (s.emode[id]) {
           const T *F = (const T *)s.eflux;
 #pragma unroll
           for (int q = 0; q < NQE; ++q) {
@@ -353,9 +381,33 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
               Fh[q][v] = minus ? -f : f;
             }
           }
+          weighted = have = true;
         }
-      } else {
+      }
+    }
+    if (!have) {
+      // own traces at the edge Gauss points and h_b there (end nodes of local edge l, vertex
+      // (l+1)%3 -> (l+2)%3, selected without dynamic register indexing)
+      const T nx = geo[(GEO_NX0 + l) * (size_t)ne + e], ny = geo[(GEO_NY0 + l) * (size_t)ne + e];
+      const T hbA = l == 0 ? hb[1] : (l == 1 ? hb[2] : hb[0]);
+      const T hbB = l == 0 ? hb[2] : (l == 1 ? hb[0] : hb[1]);
+      T wp[NQE][3], hbq[NQE];
+#pragma unroll
+      for (int q = 0; q < NQE; ++q) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          T x = 0;
+#pragma unroll
+          for (int k = 0; k < ND; ++k) x += w[v][k] * s_phe[l][q][k];
+          wp[q][v] = x;
+        }
+        hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hbA + (T(1) + tb.se[q]) * hbB);
+      }
+      bool flows = false;
+      if (j >= 0 && !SPLIT) {
         const int lj = (m.nle[e] >> (2 * l)) & 3;
+        const double hbAd = l == 0 ? hbd[1] : (l == 1 ? hbd[2] : hbd[0]);
+        const double hbBd = l == 0 ? hbd[2] : (l == 1 ? hbd[0] : hbd[1]);
         flows = edge_flows<P>(ph, fe, s.wd ? s.wd[j] : 0, s.uin, ne, e, l, j, lj, hbAd, hbBd);
         if (flows) {
           T wn[3][ND];
@@ -370,22 +422,21 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
               for (int k = 0; k < ND; ++k) x += wn[v][k] * s_phe[lj][NQE - 1 - q][k];
               wm[v] = x;
             }
-            llf(g, wp[q], wm, hbq[q], nx, ny, Fh[q]);
+            llf(g, sqg, wp[q], wm, hbq[q], nx, ny, Fh[q]);
           }
         }
       }
-      if (!flows)
+      if (j == NBR_OPEN) {
+        const double ts = stage_time(s.clk, s.stage, s.tide_t);
+        const T zt = from_d<T>(ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase));
 #pragma unroll
-        for (int q = 0; q < NQE; ++q) wall(g, wp[q], hbq[q], nx, ny, Fh[q]);
-    } else if (j == NBR_LAND) {
+        for (int q = 0; q < NQE; ++q) {
+          const T wo[3] = {zt, wp[q][1], wp[q][2]};
+          llf(g, sqg, wp[q], wo, hbq[q], nx, ny, Fh[q]);
+        }
+      } else if (!flows) {  // land boundary, or an interior edge closed by wetting/drying
 #pragma unroll
-      for (int q = 0; q < NQE; ++q) wall(g, wp[q], hbq[q], nx, ny, Fh[q]);
-    } else {
-      const T zt = (T)(ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase));
-#pragma unroll
-      for (int q = 0; q < NQE; ++q) {
-        const T wo[3] = {zt, wp[q][1], wp[q][2]};
-        llf(g, wp[q], wo, hbq[q], nx, ny, Fh[q]);
+        for (int q = 0; q < NQE; ++q) wall(g, sqg, wp[q], hbq[q], nx, ny, Fh[q]);
       }
     }
 #pragma unroll
@@ -456,15 +507,16 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
       T L = r[v][k] * idJ * tb.inrm[k];
       if (k < 3) L += (v == 1) ? src1[k] : (v == 2 ? src2[k] : T(0));
       const size_t ix = (size_t)(v * ND + k) * base + e;
+      const double Ld = to_d<T>(L);
       double out;
       if (write_rhs) {
-        out = (double)L;
+        out = Ld;
       } else if (s.stage == 0) {
-        out = s.uin[ix] + dt * (double)L;
+        out = s.uin[ix] + dt * Ld;
       } else {
-        out = 0.5 * s.un[ix] + 0.5 * (s.uin[ix] + dt * (double)L);
+        out = 0.5 * s.un[ix] + 0.5 * (s.uin[ix] + dt * Ld);
       }
-      bad |= !isfinite(out);
+      bad |= !finite_bits(out);
       s.uout[ix] = out;
       if (k == 0 && s.mean) s.mean[(size_t)v * ne + e] = out;
     }
@@ -519,12 +571,12 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
     bool any = false;
 #pragma unroll 1
     for (int v = 0; v < 3; ++v) {
-      const T u0 = (T)u[(size_t)(v * ND) * ne + e];
-      const T u1 = (T)u[(size_t)(v * ND + 1) * ne + e];
-      const T u2 = (T)u[(size_t)(v * ND + 2) * ne + e];
+      const T u0 = from_d<T>(u[(size_t)(v * ND) * ne + e]);
+      const T u1 = from_d<T>(u[(size_t)(v * ND + 1) * ne + e]);
+      const T u2 = from_d<T>(u[(size_t)(v * ND + 2) * ne + e]);
       T ub[3];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) ub[j] = nb[j] >= 0 ? (T)mean[(size_t)v * ne + nb[j]] : u0;
+      for (int j = 0; j < 3; ++j) ub[j] = nb[j] >= 0 ? from_d<T>(mean[(size_t)v * ne + nb[j]]) : u0;
       T d[3];
       bool act = false;
 #pragma unroll
@@ -552,8 +604,8 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
       for (int i = 0; i < 3; ++i) dh[i] = tp * (d[i] > T(0) ? d[i] : T(0)) - tm * (d[i] < T(0) ? -d[i] : T(0));
       // linear function with deviations dh at the midpoints of local edges 0 and 1
       const T det = tb.phm[0][1] * tb.phm[1][2] - tb.phm[0][2] * tb.phm[1][1];
-      u[(size_t)(v * ND + 1) * ne + e] = (double)((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) / det);
-      u[(size_t)(v * ND + 2) * ne + e] = (double)((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) / det);
+      u[(size_t)(v * ND + 1) * ne + e] = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) / det);
+      u[(size_t)(v * ND + 2) * ne + e] = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) / det);
     }
     if constexpr (P == 2) {
       if (any)
@@ -566,12 +618,26 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
     const double h0 = ph.h0;
     const double hbv[3] = {m.hbv[e], m.hbv[ne + e], m.hbv[2 * (size_t)ne + e]};
     const double z0 = u[e], z1 = u[(size_t)ne + e], z2 = u[2 * (size_t)ne + e];
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // Mixed form: a float evaluation decides the clearly wet elements (every vertex depth
+      // exceeds h0 by more than the float rounding of its terms); only the rest are tested in double.
+      const float fz0 = d2f(z0), fz1 = d2f(z1), fz2 = d2f(z2);
+      const float fh0 = d2f(hbv[0]), fh1 = d2f(hbv[1]), fh2 = d2f(hbv[2]);
+      const float mag = fabsf(fz0) + fabsf(fz1) + 2.f * fabsf(fz2) + fmaxf(fabsf(fh0), fmaxf(fabsf(fh1), fabsf(fh2)));
+      const float margin = 1e-6f * mag + 1e-6f;
+      const float lo = fminf(fz0 - fz1 - fz2 + fh0, fminf(fz0 + fz1 - fz2 + fh1, fz0 + 2.f * fz2 + fh2));
+      if (lo > (float)h0 + margin) {
+        if (do_wd == 1 || do_wd == 2) wd[e] = 0;
+        return;
+      }
+    }
     // zeta at the reference vertices (-1,-1), (1,-1), (-1,1): psi_10 = (-1, 1, 0), psi_01 = (-1, -1, 2)
     double H[3] = {z0 - z1 - z2 + hbv[0], z0 + z1 - z2 + hbv[1], z0 + 2.0 * z2 + hbv[2]};
-    const double Hm = (H[0] + H[1] + H[2]) / 3.0;
+    const double Hs = H[0] + H[1] + H[2];  // 3 x mean depth
     int flag;
     bool changed = false;
-    if (Hm <= h0 + WD_TOL) {
+    if (Hs <= 3.0 * (h0 + WD_TOL)) {
+      const double Hm = Hs / 3.0;
       H[0] = H[1] = H[2] = Hm;
       flag = 2;
       changed = true;
@@ -582,7 +648,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
 #pragma unroll
         for (int i = 0; i < 3; ++i)
           if (H[i] >= h0) ex += H[i] - h0;
-        const double S = (3.0 * Hm - 3.0 * h0) / ex;
+        const double S = (Hs - 3.0 * h0) / ex;
 #pragma unroll
         for (int i = 0; i < 3; ++i) H[i] = (H[i] < h0) ? h0 : h0 + (H[i] - h0) * S;
         changed = true;
@@ -614,7 +680,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
           for (int k = 3; k < ND; ++k) u[(size_t)(v * ND + k) * ne + e] = 0.0;
     }
     wd[e] = (uint8_t)flag;
-    if (Hm < 0.0) atomicOr(err, ERR_NEGDEPTH);
+    if (Hs < 0.0) atomicOr(err, ERR_NEGDEPTH);
   }
 }
 
