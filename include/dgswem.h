@@ -77,6 +77,10 @@ extern "C" {
                                   atomic-free) */
 #define DGSWEM_VARIANT_FUSED 2 /* one element kernel computes its own edge fluxes from its
                                   neighbours' states (no flux scratch, edge work done twice) */
+#define DGSWEM_VARIANT_TILED 3 /* one block per tile of consecutive elements: the tile's states
+                                  are staged in shared memory, every edge touching the tile is
+                                  computed once by the block (edges between tiles by both), then
+                                  each thread finishes its element (no flux scratch in HBM) */
 
 typedef struct dgswem_ctx dgswem_ctx; /* opaque, library-owned */
 
@@ -113,7 +117,8 @@ typedef struct {
 /* Tuning knobs; pass NULL to dgswem_create for the defaults (all zero = automatic). */
 typedef struct {
   int32_t variant;   /* DGSWEM_VARIANT_* */
-  int32_t block;     /* threads per block of the element kernels: 0 (auto), 64, 128, 256 */
+  int32_t block;     /* threads per block of the element kernels (= elements per tile for the
+                        tiled variant): 0 (auto), 64, 128, 256 */
   int32_t reorder;   /* 0: auto (Hilbert order on), 1: Hilbert curve order, 2: keep caller order */
   int32_t autotune;  /* 1: time the candidate variants / block sizes at attach and keep the best */
 } dgswem_tuning;

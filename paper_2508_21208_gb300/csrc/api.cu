@@ -89,6 +89,8 @@ void upload_all_tables() {
   upload_tables_f64(td);
   upload_tables_f32(td);
   upload_common_tables(td);
+  prepare_tile_f64();
+  prepare_tile_f32();
 }
 
 // Convert a double vector to the arithmetic type of the form (float for the mixed form).
@@ -151,7 +153,47 @@ static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
   c->step = k.take<long long>(1);
   c->err = k.take<int>(1);
   c->dtbits = k.take<unsigned long long>(1);
+  // tile edge lists, sized for the smallest tile (64) and the worst case of the edge count
+  const int mt = max_tile_edges(H);
+  DevTiles &T = c->tiles;
+  T.start = k.take<int>((ne + 63) / 64 + 1);
+  T.ea = k.take<int>(mt);
+  T.eb = k.take<int>(mt);
+  T.code = k.take<uint8_t>(mt);
+  T.geo = k.take<char>(tsz * 3 * mt);
+  T.hb = k.take<double>(2 * (size_t)mt);
   *bytes = k.off;
+}
+
+// Build and upload the tile edge lists for tile size `tile` (outside any stream capture).
+static int prepare_tiles(dgswem_ctx *c, int tile) {
+  if (c->tiles.tile == tile) return 0;
+  TileEdges &H = c->htiles;
+  build_tile_edges(c->hm, tile, H);
+  DevTiles &T = c->tiles;
+  const int mt = max_tile_edges(c->hm);
+  if (H.n > mt) return ctx_fail(c, DGSWEM_EINVAL, "tile edge list larger than its buffer");
+  c->host_keep.push_back(typed(H.geo, c->mixed));
+  cudaStream_t s = c->st;
+  int r = 0;
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(T.start), H.start.data(), H.start.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, s), "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(T.ea), H.ea.data(), H.n * sizeof(int), cudaMemcpyHostToDevice, s),
+                "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(T.eb), H.eb.data(), H.n * sizeof(int), cudaMemcpyHostToDevice, s),
+                "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<uint8_t *>(T.code), H.code.data(), H.n, cudaMemcpyHostToDevice, s),
+                "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(T.geo), c->host_keep.back().data(), c->host_keep.back().size(),
+                                   cudaMemcpyHostToDevice, s), "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<double *>(T.hb), H.hb.data(), H.hb.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice, s), "tiles");
+  if (r) return c->sticky;
+  if (int e = ctx_cuda(c, cudaStreamSynchronize(s), "tiles sync")) return e;
+  T.tile = tile;
+  T.ntiles = H.ntiles;
+  T.n = H.n;
+  return 0;
 }
 
 // ------------------------------------------------------------------ one step
@@ -194,12 +236,17 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
     sa.clk = clk;
     sa.stage = stage;
     sa.err = c->err;
-    if (split && c->dm.nint > 0) {
-      mark(c, kname_edge, names, &ev_i);
-      launch_edge(c->mixed, c->P, c->dm, sa, ph, cfg);
+    if (variant == DGSWEM_VARIANT_TILED) {
+      mark(c, kname_element, names, &ev_i);
+      launch_tile(c->mixed, c->P, false, c->dm, c->tiles, sa, ph, cfg);
+    } else {
+      if (split && c->dm.nint > 0) {
+        mark(c, kname_edge, names, &ev_i);
+        launch_edge(c->mixed, c->P, c->dm, sa, ph, cfg);
+      }
+      mark(c, kname_element, names, &ev_i);
+      launch_element(c->mixed, c->P, split, false, c->dm, sa, ph, cfg);
     }
-    mark(c, kname_element, names, &ev_i);
-    launch_element(c->mixed, c->P, split, false, c->dm, sa, ph, cfg);
     if (ph.limiter || ph.wetdry) {
       mark(c, kname_limwd, names, &ev_i);
       launch_limwd(c->mixed, c->P, ph.limiter, ph.wetdry, c->dm, out, c->mean, c->wd, ph, c->err, cfg);
@@ -228,6 +275,8 @@ static void destroy_graph(dgswem_ctx *c) {
 
 int capture_graph(dgswem_ctx *c, int variant, int block, bool timing) {
   destroy_graph(c);
+  if (!c->ensemble && variant == DGSWEM_VARIANT_TILED)
+    if (int r = prepare_tiles(c, block)) return r;
   std::vector<const char *> names;
   if (timing) {
     const int need = kernels_in_step(c, variant) + 1;
@@ -330,7 +379,7 @@ int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_par
   dgswem_ctx *c = new dgswem_ctx();
   c->prm = *params;
   if (tuning) c->tun = *tuning;
-  if (c->tun.variant < 0 || c->tun.variant > 2 || (c->tun.block != 0 && c->tun.block != 64 && c->tun.block != 128 &&
+  if (c->tun.variant < 0 || c->tun.variant > 3 || (c->tun.block != 0 && c->tun.block != 64 && c->tun.block != 128 &&
                                                     c->tun.block != 256) ||
       c->tun.reorder < 0 || c->tun.reorder > 2) {
     delete c;
@@ -382,7 +431,7 @@ static int upload_static(dgswem_ctx *c) {
 static int autotune(dgswem_ctx *c, int *best_variant, int *best_block) {
   std::vector<int> variants, blocks;
   if (c->tun.variant == DGSWEM_VARIANT_AUTO)
-    variants = {DGSWEM_VARIANT_SPLIT, DGSWEM_VARIANT_FUSED};
+    variants = {DGSWEM_VARIANT_SPLIT, DGSWEM_VARIANT_FUSED, DGSWEM_VARIANT_TILED};
   else
     variants = {c->tun.variant};
   if (c->tun.block == 0)
@@ -440,6 +489,7 @@ int dgswem_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream) 
   layout(c, c->ws, &sz);
   cudaStream_t s = c->st;
   if (int r = upload_static(c)) return r;
+  c->tiles.tile = 0;
   const size_t nu = 3 * (size_t)c->ND * c->hm.ne;
   cudaMemsetAsync(c->step, 0, sizeof(long long), s);
   cudaMemsetAsync(c->err, 0, sizeof(int), s);
@@ -607,8 +657,12 @@ int dgswem_eval_rhs(dgswem_ctx *c, double t, double *h_out) {
   sa.err = c->err;
   sa.tide_t = t;
   const bool split = c->variant == DGSWEM_VARIANT_SPLIT;
-  if (split) launch_edge(c->mixed, c->P, c->dm, sa, c->ph, cfg);
-  launch_element(c->mixed, c->P, split, true, c->dm, sa, c->ph, cfg);
+  if (c->variant == DGSWEM_VARIANT_TILED) {
+    launch_tile(c->mixed, c->P, true, c->dm, c->tiles, sa, c->ph, cfg);
+  } else {
+    if (split) launch_edge(c->mixed, c->P, c->dm, sa, c->ph, cfg);
+    launch_element(c->mixed, c->P, split, true, c->dm, sa, c->ph, cfg);
+  }
   const int ne = c->hm.ne, ND = c->ND;
   launch_permute(c->U1, c->staging, c->d_iperm, 3 * ND, ne, c->st);
   if (int r = ctx_cuda(c, cudaMemcpyAsync(h_out, c->staging, 3 * (size_t)ND * ne * sizeof(double), cudaMemcpyDeviceToHost,

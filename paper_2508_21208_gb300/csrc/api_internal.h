@@ -44,6 +44,8 @@ struct dgswem_ctx {
   cudaStream_t st = nullptr, own_stream = nullptr;
   bool attached = false;
   dg::DevMesh dm{};
+  dg::DevTiles tiles{};     // tile edge lists of the tiled variant (tile size tiles.tile, 0 = none)
+  dg::TileEdges htiles;
   dg::Phys ph{};
   int *d_perm = nullptr, *d_iperm = nullptr;
   double *U0 = nullptr, *U1 = nullptr, *mean = nullptr, *partial = nullptr, *result = nullptr,

@@ -53,6 +53,21 @@ struct HostMesh {
   std::vector<double> nodexy;     // [2][nn]
 };
 
+// Edges touching each tile of `tile` consecutive (internal-order) elements, for the tiled
+// element kernel: an interior edge whose two elements lie in one tile is listed once there; an
+// edge between two tiles is listed in both; a boundary edge in its element's tile.  Side A is the
+// edge's plus side (the normal points out of A); B is the minus element or NBR_LAND / NBR_OPEN.
+struct TileEdges {
+  int tile = 0, ntiles = 0, n = 0;
+  std::vector<int> start;     // [ntiles + 1]
+  std::vector<int> ea, eb;    // [n] elements (or boundary code in eb)
+  std::vector<uint8_t> code;  // [n] lA | lB << 2 | (A in tile) << 4 | (B in tile) << 5
+  std::vector<double> geo;    // [3][n] nx, ny, half length
+  std::vector<double> hb;     // [2][n] h_b at the edge's end nodes (A's counter-clockwise order)
+};
+void build_tile_edges(const HostMesh &H, int tile, TileEdges &out);
+inline int max_tile_edges(const HostMesh &H) { return 2 * H.nint + H.nbnd; }
+
 // Returns 0 or DGSWEM_EMESH / DGSWEM_EINVAL with a message.
 int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, HostMesh &out,
                     std::string &msg);
@@ -82,6 +97,16 @@ struct DevMesh {
   const void *edgeo;       // T [3][nint]
   const double *edhb;      // [2][nint]
   const double *nodexy;    // [2][nn]
+};
+
+struct DevTiles {
+  int tile, ntiles;
+  const int *start;        // [ntiles + 1]
+  const int *ea, *eb;      // [n]
+  const uint8_t *code;     // [n]
+  const void *geo;         // T [3][n]
+  const double *hb;        // [2][n]
+  int n;
 };
 
 struct Clock {
@@ -168,6 +193,9 @@ struct LaunchCfg {
   void launch_limwd_##SUF(int p, bool do_lim, int do_wd, const DevMesh &m, double *u,            \
                           const double *mean, uint8_t *wd, const Phys &ph, int *err,             \
                           const LaunchCfg &c);                                                   \
+  void launch_tile_##SUF(int p, bool write_rhs, const DevMesh &m, const DevTiles &tl,              \
+                         const StageArgs &s, const Phys &ph, const LaunchCfg &c);                 \
+  void prepare_tile_##SUF();                                                                      \
   cudaError_t launch_ensemble_##SUF(int p, bool persistent, const EnsArgs &a, int block, int grid, \
                                     cudaStream_t s);                                             \
   int ensemble_blocks_per_sm_##SUF(int p, int block);
@@ -194,6 +222,10 @@ inline void launch_limwd(bool mixed, int p, bool do_lim, int do_wd, const DevMes
                          const LaunchCfg &c) {
   mixed ? launch_limwd_f32(p, do_lim, do_wd, m, u, mean, wd, ph, err, c)
         : launch_limwd_f64(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
+}
+inline void launch_tile(bool mixed, int p, bool write_rhs, const DevMesh &m, const DevTiles &tl,
+                        const StageArgs &s, const Phys &ph, const LaunchCfg &c) {
+  mixed ? launch_tile_f32(p, write_rhs, m, tl, s, ph, c) : launch_tile_f64(p, write_rhs, m, tl, s, ph, c);
 }
 inline cudaError_t launch_ensemble(bool mixed, int p, bool persistent, const EnsArgs &a, int block, int grid,
                                    cudaStream_t s) {

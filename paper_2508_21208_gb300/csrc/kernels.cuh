@@ -269,29 +269,44 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
 // Source terms linear in the state (bathymetry slope g zeta dh_b/dx, Coriolis, wind stress,
 // pressure gradient -H dp_a/dx with linear p_a) are integrated in closed form through the basis
 // orthogonality; the area rule is exact for them, so this is the same discrete operator.
-template <int P, typename T, bool SPLIT>
-__device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &s, const Phys &ph,
-                                             const int write_rhs, const int e,
-                                             const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
-  constexpr int ND = nd_of(P), NQA = nqa_of(P), NQE = nqe_of(P);
-  const Tab<T> &tb = ctab<T>(P);
+// Per-element quantities shared by the element-update variants.
+template <int P, typename T>
+struct ElemCtx {
+  T w[3][nd_of(P)];
+  T rx, ry, sx, sy, dJ;
+  double hbd[3];
+  T hb[3];
+};
+
+template <int P, typename T>
+__device__ __forceinline__ void elem_load(const DevMesh &m, const double *u, int e, ElemCtx<P, T> &c) {
   const int ne = m.ne;
-  const T g = (T)ph.g, sqg = (T)ph.sqrt_g;
-  T w[3][ND];
-  load_modes<P, T>(s.uin, ne, e, w);
+  load_modes<P, T>(u, ne, e, c.w);
   const T *geo = (const T *)m.geo;
-  const T rx = geo[GEO_RX * (size_t)ne + e], ry = geo[GEO_RY * (size_t)ne + e];
-  const T sx = geo[GEO_SX * (size_t)ne + e], sy = geo[GEO_SY * (size_t)ne + e];
-  const T dJ = geo[GEO_DETJ * (size_t)ne + e];
-  const double hbd[3] = {m.hbv[e], m.hbv[ne + e], m.hbv[2 * (size_t)ne + e]};
-  const T hb[3] = {from_d<T>(hbd[0]), from_d<T>(hbd[1]), from_d<T>(hbd[2])};
-  T r[3][ND];
+  c.rx = geo[GEO_RX * (size_t)ne + e];
+  c.ry = geo[GEO_RY * (size_t)ne + e];
+  c.sx = geo[GEO_SX * (size_t)ne + e];
+  c.sy = geo[GEO_SY * (size_t)ne + e];
+  c.dJ = geo[GEO_DETJ * (size_t)ne + e];
+  c.hbd[0] = m.hbv[e];
+  c.hbd[1] = m.hbv[ne + e];
+  c.hbd[2] = m.hbv[2 * (size_t)ne + e];
+  for (int a = 0; a < 3; ++a) c.hb[a] = from_d<T>(c.hbd[a]);
+}
+
+// Area integrals (Alg. 1): advective + pressure flux and friction, r_k set (not accumulated).
+template <int P, typename T>
+__device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph, T r[3][nd_of(P)]) {
+  constexpr int ND = nd_of(P), NQA = nqa_of(P);
+  const Tab<T> &tb = ctab<T>(P);
+  const T g = (T)ph.g;
+  const T rx = c.rx, ry = c.ry, sx = c.sx, sy = c.sy, dJ = c.dJ;
+  const T (&w)[3][ND] = c.w;
+  const T (&hb)[3] = c.hb;
 #pragma unroll
   for (int v = 0; v < 3; ++v)
 #pragma unroll
     for (int k = 0; k < ND; ++k) r[v][k] = T(0);
-
-  // ---------------- area integrals (Alg. 1): advective + pressure flux and friction
   {
     T fr[2][ND];
 #pragma unroll
@@ -355,6 +370,109 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
       r[2][k] = (r[2][k] - fr[1][k]) * dJ;
     }
   }
+
+}
+
+// Inverse mass matrix, closed-form linear sources and the RK stage; writes u^(s+1) and the means.
+template <int P, typename T>
+__device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s, const Phys &ph,
+                                            const int write_rhs, const int e, const ElemCtx<P, T> &c,
+                                            T r[3][nd_of(P)]) {
+  constexpr int ND = nd_of(P);
+  const Tab<T> &tb = ctab<T>(P);
+  const int ne = m.ne;
+  const T g = (T)ph.g;
+  const T rx = c.rx, ry = c.ry, sx = c.sx, sy = c.sy, dJ = c.dJ;
+  const T (&w)[3][ND] = c.w;
+  const T (&hb)[3] = c.hb;
+  const T idJ = T(1) / dJ;
+  T src1[3] = {0, 0, 0}, src2[3] = {0, 0, 0};  // per linear mode, for q_x and q_y
+  {
+    const T hbx = T(0.5) * (rx * (hb[1] - hb[0]) + sx * (hb[2] - hb[0]));
+    const T hby = T(0.5) * (ry * (hb[1] - hb[0]) + sy * (hb[2] - hb[0]));
+    const T fc = (T)ph.fcor;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      src1[k] = g * hbx * w[0][k] + fc * w[2][k];
+      src2[k] = g * hby * w[0][k] - fc * w[1][k];
+    }
+    if (s.frc) {
+      const T *F = (const T *)s.frc;
+      const int nn = m.nn;
+      const int n0 = m.vnode[e], n1 = m.vnode[ne + e], n2 = m.vnode[2 * (size_t)ne + e];
+      const T t0 = F[n0], t1 = F[n1], t2 = F[n2];
+      const T u0 = F[nn + n0], u1 = F[nn + n1], u2 = F[nn + n2];
+      const T p0 = F[2 * nn + n0], p1 = F[2 * nn + n1], p2 = F[2 * nn + n2];
+      const T pax = T(0.5) * (rx * (p1 - p0) + sx * (p2 - p0));
+      const T pay = T(0.5) * (ry * (p1 - p0) + sy * (p2 - p0));
+      // Dubiner linear modes of the interpolant through vertex values (a0, a1, a2)
+      const T hm[3] = {(hb[0] + hb[1] + hb[2]) / T(3), T(0.5) * (hb[1] - hb[0]),
+                       (T(2) * hb[2] - hb[0] - hb[1]) / T(6)};
+      const T tm[3] = {(t0 + t1 + t2) / T(3), T(0.5) * (t1 - t0), (T(2) * t2 - t0 - t1) / T(6)};
+      const T um[3] = {(u0 + u1 + u2) / T(3), T(0.5) * (u1 - u0), (T(2) * u2 - u0 - u1) / T(6)};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        src1[k] += tm[k] - pax * (w[0][k] + hm[k]);
+        src2[k] += um[k] - pay * (w[0][k] + hm[k]);
+      }
+      if constexpr (P == 2) {
+        // quadratic modes: only the zeta part of -H grad p_a remains
+        for (int k = 3; k < ND; ++k) {
+          r[1][k] -= dJ * tb.nrm[k] * pax * w[0][k];
+          r[2][k] -= dJ * tb.nrm[k] * pay * w[0][k];
+        }
+      }
+    }
+    if constexpr (P == 2) {
+      for (int k = 3; k < ND; ++k) {
+        r[1][k] += dJ * tb.nrm[k] * (g * hbx * w[0][k] + fc * w[2][k]);
+        r[2][k] += dJ * tb.nrm[k] * (g * hby * w[0][k] - fc * w[1][k]);
+      }
+    }
+  }
+  const double dt = s.clk.dt;
+  const size_t base = (size_t)ne;
+  bool bad = false;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      T L = r[v][k] * idJ * tb.inrm[k];
+      if (k < 3) L += (v == 1) ? src1[k] : (v == 2 ? src2[k] : T(0));
+      const size_t ix = (size_t)(v * ND + k) * base + e;
+      const double Ld = to_d<T>(L);
+      double out;
+      if (write_rhs) {
+        out = Ld;
+      } else if (s.stage == 0) {
+        out = s.uin[ix] + dt * Ld;
+      } else {
+        out = 0.5 * s.un[ix] + 0.5 * (s.uin[ix] + dt * Ld);
+      }
+      bad |= !finite_bits(out);
+      s.uout[ix] = out;
+      if (k == 0 && s.mean) s.mean[(size_t)v * ne + e] = out;
+    }
+  }
+  if (bad) atomicOr(s.err, ERR_NONFINITE);
+}
+
+template <int P, typename T, bool SPLIT>
+__device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &s, const Phys &ph,
+                                             const int write_rhs, const int e,
+                                             const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
+  constexpr int ND = nd_of(P), NQE = nqe_of(P);
+  const Tab<T> &tb = ctab<T>(P);
+  const int ne = m.ne;
+  const T g = (T)ph.g, sqg = (T)ph.sqrt_g;
+  ElemCtx<P, T> c;
+  elem_load<P, T>(m, s.uin, e, c);
+  const T *geo = (const T *)m.geo;
+  const T (&w)[3][ND] = c.w;
+  const T (&hb)[3] = c.hb;
+  const double (&hbd)[3] = c.hbd;
+  T r[3][ND];
+  elem_area<P, T>(c, ph, r);
 
   // ---------------- edge integrals (Alg. 2 + Alg. 3), gathered per element in a fixed order
   const uint8_t fe = s.wd ? s.wd[e] : 0;
@@ -451,77 +569,7 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
     }
   }
 
-  // ---------------- inverse mass matrix, closed-form linear sources, RK stage
-  const T idJ = T(1) / dJ;
-  T src1[3] = {0, 0, 0}, src2[3] = {0, 0, 0};  // per linear mode, for q_x and q_y
-  {
-    const T hbx = T(0.5) * (rx * (hb[1] - hb[0]) + sx * (hb[2] - hb[0]));
-    const T hby = T(0.5) * (ry * (hb[1] - hb[0]) + sy * (hb[2] - hb[0]));
-    const T fc = (T)ph.fcor;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      src1[k] = g * hbx * w[0][k] + fc * w[2][k];
-      src2[k] = g * hby * w[0][k] - fc * w[1][k];
-    }
-    if (s.frc) {
-      const T *F = (const T *)s.frc;
-      const int nn = m.nn;
-      const int n0 = m.vnode[e], n1 = m.vnode[ne + e], n2 = m.vnode[2 * (size_t)ne + e];
-      const T t0 = F[n0], t1 = F[n1], t2 = F[n2];
-      const T u0 = F[nn + n0], u1 = F[nn + n1], u2 = F[nn + n2];
-      const T p0 = F[2 * nn + n0], p1 = F[2 * nn + n1], p2 = F[2 * nn + n2];
-      const T pax = T(0.5) * (rx * (p1 - p0) + sx * (p2 - p0));
-      const T pay = T(0.5) * (ry * (p1 - p0) + sy * (p2 - p0));
-      // Dubiner linear modes of the interpolant through vertex values (a0, a1, a2)
-      const T hm[3] = {(hb[0] + hb[1] + hb[2]) / T(3), T(0.5) * (hb[1] - hb[0]),
-                       (T(2) * hb[2] - hb[0] - hb[1]) / T(6)};
-      const T tm[3] = {(t0 + t1 + t2) / T(3), T(0.5) * (t1 - t0), (T(2) * t2 - t0 - t1) / T(6)};
-      const T um[3] = {(u0 + u1 + u2) / T(3), T(0.5) * (u1 - u0), (T(2) * u2 - u0 - u1) / T(6)};
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        src1[k] += tm[k] - pax * (w[0][k] + hm[k]);
-        src2[k] += um[k] - pay * (w[0][k] + hm[k]);
-      }
-      if constexpr (P == 2) {
-        // quadratic modes: only the zeta part of -H grad p_a remains
-        for (int k = 3; k < ND; ++k) {
-          r[1][k] -= dJ * tb.nrm[k] * pax * w[0][k];
-          r[2][k] -= dJ * tb.nrm[k] * pay * w[0][k];
-        }
-      }
-    }
-    if constexpr (P == 2) {
-      for (int k = 3; k < ND; ++k) {
-        r[1][k] += dJ * tb.nrm[k] * (g * hbx * w[0][k] + fc * w[2][k]);
-        r[2][k] += dJ * tb.nrm[k] * (g * hby * w[0][k] - fc * w[1][k]);
-      }
-    }
-  }
-  const double dt = s.clk.dt;
-  const size_t base = (size_t)ne;
-  bool bad = false;
-#pragma unroll
-  for (int v = 0; v < 3; ++v) {
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-      T L = r[v][k] * idJ * tb.inrm[k];
-      if (k < 3) L += (v == 1) ? src1[k] : (v == 2 ? src2[k] : T(0));
-      const size_t ix = (size_t)(v * ND + k) * base + e;
-      const double Ld = to_d<T>(L);
-      double out;
-      if (write_rhs) {
-        out = Ld;
-      } else if (s.stage == 0) {
-        out = s.uin[ix] + dt * Ld;
-      } else {
-        out = 0.5 * s.un[ix] + 0.5 * (s.uin[ix] + dt * Ld);
-      }
-      bad |= !finite_bits(out);
-      s.uout[ix] = out;
-      if (k == 0 && s.mean) s.mean[(size_t)v * ne + e] = out;
-    }
-  }
-  if (bad) atomicOr(s.err, ERR_NONFINITE);
+  elem_finish<P, T>(m, s, ph, write_rhs, e, c, r);
 }
 
 template <int P, typename T, bool SPLIT>
@@ -533,6 +581,165 @@ __global__ void __launch_bounds__(256)
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m.ne) return;
   element_body<P, T, SPLIT>(m, s, ph, write_rhs, e, s_phe);
+}
+
+// ------------------------------------------------------------------------ tiled element update
+// One block per tile of `tl.tile` consecutive elements (Hilbert order keeps a tile compact).  The
+// tile's states are staged in shared memory; the block's threads compute every edge touching the
+// tile once (an edge between two tiles is computed identically by both) and leave the weighted
+// flux of each (element, local edge, Gauss point) in shared memory; after one barrier each thread
+// finishes its element (area integrals, gather in the fixed local-edge order, inverse mass, RK).
+// Shared memory: double state [3*ND][tile], float/double flux slots [3][NQE][3][tile], flags.
+template <int P, typename T>
+__host__ __device__ constexpr size_t tile_smem_bytes(int tile) {
+  return sizeof(double) * 3 * nd_of(P) * tile + sizeof(T) * 9 * nqe_of(P) * tile + tile;
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void tile_modes(const double *s_ud, int B, const double *u, int ne, int e, bool local,
+                                           int li, T w[3][nd_of(P)]) {
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int k = 0; k < nd_of(P); ++k) {
+      const int row = v * nd_of(P) + k;
+      w[v][k] = from_d<T>(local ? s_ud[row * B + li] : __ldg(&u[(size_t)row * ne + e]));
+    }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, const StageArgs &s, const Phys &ph,
+                                          const int x, const int e0, const double *s_ud, T *s_slot,
+                                          const uint8_t *s_wd, const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
+  constexpr int ND = nd_of(P), NQE = nqe_of(P);
+  const Tab<T> &tb = ctab<T>(P);
+  const int B = tl.tile, ne = m.ne;
+  const T g = (T)ph.g, sqg = (T)ph.sqrt_g;
+  const int a = tl.ea[x], b = tl.eb[x];
+  const unsigned code = tl.code[x];
+  const int la = code & 3u, lb = (code >> 2) & 3u;
+  const bool ina = (code >> 4) & 1u, inb = (code >> 5) & 1u;
+  const T *tg = (const T *)tl.geo;
+  const T nx = tg[x], ny = tg[tl.n + x], hl = tg[2 * (size_t)tl.n + x];
+  const double hAd = tl.hb[x], hBd = tl.hb[tl.n + x];
+  const T hA = from_d<T>(hAd), hB = from_d<T>(hBd);
+  T wa[3][ND];
+  tile_modes<P, T>(s_ud, B, s.uin, ne, a, ina, a - e0, wa);
+  T ta[NQE][3], hbq[NQE];
+#pragma unroll
+  for (int q = 0; q < NQE; ++q) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < ND; ++k) acc += wa[v][k] * s_phe[la][q][k];
+      ta[q][v] = acc;
+    }
+    hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hA + (T(1) + tb.se[q]) * hB);
+  }
+  // slot of (element li, local edge l, Gauss point q, variable v)
+  auto slot = [&](int li, int l, int q, int v) -> T & { return s_slot[(size_t)((l * NQE + q) * 3 + v) * B + li]; };
+  if (b >= 0) {
+    const uint8_t fa = s.wd ? (ina ? s_wd[a - e0] : s.wd[a]) : 0;
+    const uint8_t fb = s.wd ? (inb ? s_wd[b - e0] : s.wd[b]) : 0;
+    const bool flows = edge_flows<P>(ph, fa, fb, s.uin, ne, a, la, b, lb, hAd, hBd);
+    T wb[3][ND];
+    tile_modes<P, T>(s_ud, B, s.uin, ne, b, inb, b - e0, wb);
+#pragma unroll
+    for (int q = 0; q < NQE; ++q) {
+      T tbq[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        T acc = 0;
+#pragma unroll
+        for (int k = 0; k < ND; ++k) acc += wb[v][k] * s_phe[lb][NQE - 1 - q][k];
+        tbq[v] = acc;
+      }
+      const T wgt = hl * tb.we[q];
+      if (flows) {
+        T f[3];
+        llf(g, sqg, ta[q], tbq, hbq[q], nx, ny, f);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          if (ina) slot(a - e0, la, q, v) = wgt * f[v];
+          if (inb) slot(b - e0, lb, NQE - 1 - q, v) = -(wgt * f[v]);
+        }
+      } else {  // closed by wetting/drying: each side sees a wall
+        if (ina) {
+          T f[3];
+          wall(g, sqg, ta[q], hbq[q], nx, ny, f);
+#pragma unroll
+          for (int v = 0; v < 3; ++v) slot(a - e0, la, q, v) = wgt * f[v];
+        }
+        if (inb) {
+          T f[3];
+          wall(g, sqg, tbq, hbq[q], -nx, -ny, f);
+#pragma unroll
+          for (int v = 0; v < 3; ++v) slot(b - e0, lb, NQE - 1 - q, v) = wgt * f[v];
+        }
+      }
+    }
+  } else if (b == NBR_LAND) {
+#pragma unroll
+    for (int q = 0; q < NQE; ++q) {
+      T f[3];
+      wall(g, sqg, ta[q], hbq[q], nx, ny, f);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) slot(a - e0, la, q, v) = hl * tb.we[q] * f[v];
+    }
+  } else {
+    const double ts = stage_time(s.clk, s.stage, s.tide_t);
+    const T zt = from_d<T>(ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase));
+#pragma unroll
+    for (int q = 0; q < NQE; ++q) {
+      const T wo[3] = {zt, ta[q][1], ta[q][2]};
+      T f[3];
+      llf(g, sqg, ta[q], wo, hbq[q], nx, ny, f);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) slot(a - e0, la, q, v) = hl * tb.we[q] * f[v];
+    }
+  }
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(256)
+    k_tile(const DevMesh m, const DevTiles tl, const StageArgs s, const Phys ph, const int write_rhs) {
+  constexpr int ND = nd_of(P), NQE = nqe_of(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T s_phe[3][NQE][ND];
+  const int B = tl.tile, ne = m.ne;
+  double *s_ud = reinterpret_cast<double *>(smem_raw);
+  T *s_slot = reinterpret_cast<T *>(s_ud + (size_t)3 * ND * B);
+  uint8_t *s_wd = reinterpret_cast<uint8_t *>(s_slot + (size_t)9 * NQE * B);
+  load_phe<P, T>(s_phe);
+  const int e0 = blockIdx.x * B, i = threadIdx.x;
+  const int nloc = min(B, ne - e0);
+  if (i < nloc) {
+#pragma unroll
+    for (int r = 0; r < 3 * ND; ++r) s_ud[r * B + i] = __ldg(&s.uin[(size_t)r * ne + e0 + i]);
+    s_wd[i] = s.wd ? s.wd[e0 + i] : 0;
+  }
+  __syncthreads();
+  const int beg = tl.start[blockIdx.x], end = tl.start[blockIdx.x + 1];
+  for (int x = beg + i; x < end; x += B) tile_edge<P, T>(m, tl, s, ph, x, e0, s_ud, s_slot, s_wd, s_phe);
+  __syncthreads();
+  if (i >= nloc) return;
+  const int e = e0 + i;
+  ElemCtx<P, T> c;
+  elem_load<P, T>(m, s.uin, e, c);
+  T r[3][ND];
+  elem_area<P, T>(c, ph, r);
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int q = 0; q < NQE; ++q)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const T f = s_slot[(size_t)((l * NQE + q) * 3 + v) * B + i];
+#pragma unroll
+        for (int k = 0; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
+      }
+  elem_finish<P, T>(m, s, ph, write_rhs, e, c, r);
 }
 
 // ------------------------------------------------------------------------ SLOPELIM + WETDRY
@@ -569,7 +776,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
     const unsigned code = m.limj[e];
     const T *A = (const T *)m.lima;
     bool any = false;
-#pragma unroll 1
+#pragma unroll
     for (int v = 0; v < 3; ++v) {
       const T u0 = from_d<T>(u[(size_t)(v * ND) * ne + e]);
       const T u1 = from_d<T>(u[(size_t)(v * ND + 1) * ne + e]);
@@ -910,6 +1117,26 @@ void launch_element_t(int p, bool split, bool write_rhs, const DevMesh &m, const
     else
       k_element<2, T, false><<<nb, c.block, 0, c.stream>>>(m, s, ph, wr);
   }
+}
+
+template <typename T>
+void launch_tile_t(int p, bool write_rhs, const DevMesh &m, const DevTiles &tl, const StageArgs &s, const Phys &ph,
+                   const LaunchCfg &c) {
+  const int wr = write_rhs ? 1 : 0;
+  if (p == 1) {
+    const size_t sm = tile_smem_bytes<1, T>(tl.tile);
+    k_tile<1, T><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
+  } else {
+    const size_t sm = tile_smem_bytes<2, T>(tl.tile);
+    k_tile<2, T><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
+  }
+}
+
+template <typename T>
+void prepare_tile_t() {
+  // allow the largest tile's dynamic shared memory (p = 2, 256 elements)
+  cudaFuncSetAttribute(k_tile<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256));
+  cudaFuncSetAttribute(k_tile<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256));
 }
 
 template <typename T>

@@ -291,6 +291,66 @@ int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, Hos
   return 0;
 }
 
+void build_tile_edges(const HostMesh &H, int tile, TileEdges &T) {
+  const int ne = H.ne, nint = H.nint;
+  T.tile = tile;
+  T.ntiles = (ne + tile - 1) / tile;
+  std::vector<int> count(T.ntiles + 1, 0);
+  auto tile_of = [&](int e) { return e / tile; };
+  for (int d = 0; d < nint; ++d) {
+    const int a = H.edel[d], b = H.edel[nint + d];
+    count[tile_of(a)]++;
+    if (tile_of(b) != tile_of(a)) count[tile_of(b)]++;
+  }
+  for (int l = 0; l < 3; ++l)
+    for (int e = 0; e < ne; ++e)
+      if (H.nbr[(size_t)l * ne + e] < 0) count[tile_of(e)]++;
+  T.start.assign(T.ntiles + 1, 0);
+  for (int t = 0; t < T.ntiles; ++t) T.start[t + 1] = T.start[t] + count[t];
+  T.n = T.start[T.ntiles];
+  T.ea.assign(T.n, 0);
+  T.eb.assign(T.n, 0);
+  T.code.assign(T.n, 0);
+  T.geo.assign(3 * (size_t)T.n, 0.0);
+  T.hb.assign(2 * (size_t)T.n, 0.0);
+  std::vector<int> fill(T.start.begin(), T.start.end() - 1);
+  auto put = [&](int t, int a, int b, int la, int lb, bool ina, bool inb, double nx, double ny, double hl, double ha,
+                 double hbb) {
+    const int i = fill[t]++;
+    T.ea[i] = a;
+    T.eb[i] = b;
+    T.code[i] = (uint8_t)(la | (lb << 2) | ((ina ? 1 : 0) << 4) | ((inb ? 1 : 0) << 5));
+    T.geo[i] = nx;
+    T.geo[(size_t)T.n + i] = ny;
+    T.geo[2 * (size_t)T.n + i] = hl;
+    T.hb[i] = ha;
+    T.hb[(size_t)T.n + i] = hbb;
+  };
+  for (int d = 0; d < nint; ++d) {
+    const int a = H.edel[d], b = H.edel[nint + d];
+    const int la = H.edle[d] & 3, lb = H.edle[d] >> 2;
+    const double nx = H.edgeo[d], ny = H.edgeo[nint + d], hl = H.edgeo[2 * (size_t)nint + d];
+    const double ha = H.edhb[d], hbb = H.edhb[nint + d];
+    const int ta = tile_of(a), tb = tile_of(b);
+    if (ta == tb) {
+      put(ta, a, b, la, lb, true, true, nx, ny, hl, ha, hbb);
+    } else {
+      put(ta, a, b, la, lb, true, false, nx, ny, hl, ha, hbb);
+      put(tb, a, b, la, lb, false, true, nx, ny, hl, ha, hbb);
+    }
+  }
+  const double *g = H.geo.data();
+  for (int e = 0; e < ne; ++e)
+    for (int l = 0; l < 3; ++l) {
+      const int code = H.nbr[(size_t)l * ne + e];
+      if (code >= 0) continue;
+      // end nodes of local edge l: vertices (l+1)%3 and (l+2)%3
+      const double ha = H.hbv[(size_t)((l + 1) % 3) * ne + e], hbb = H.hbv[(size_t)((l + 2) % 3) * ne + e];
+      put(tile_of(e), e, code, l, 0, true, false, g[(GEO_NX0 + l) * (size_t)ne + e], g[(GEO_NY0 + l) * (size_t)ne + e],
+          g[(GEO_HL0 + l) * (size_t)ne + e], ha, hbb);
+    }
+}
+
 // ------------------------------------------------------------------ reference tables
 // Dubiner basis (Sec. 2.2, Eq. dubiner) psi_ij = P_i(a) ((1-b)/2)^i P_j^(2i+1,0)(b), written out
 // for i + j <= 2, with its reference gradient.

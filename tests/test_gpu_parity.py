@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_2508_21208_gb300 import Model, synth
-from paper_2508_21208_gb300.dgswem import VARIANT_FUSED, VARIANT_SPLIT
+from paper_2508_21208_gb300.dgswem import VARIANT_FUSED, VARIANT_SPLIT, VARIANT_TILED
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def test_dt_matches_oracle(name):
     assert np.max(rel_l2(g.state(), o.state())) <= 1e-14
 
 
-@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED])
+@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED])
 @pytest.mark.parametrize("name", list(CASES))
 def test_rhs_parity(name, variant):
     c = CASES[name]()
@@ -128,10 +128,11 @@ def run_pair(c, steps, variant, block=128, p=None):
     return g, o
 
 
-@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED])
-def test_config1_200_steps(variant):
+@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED])
+@pytest.mark.parametrize("block", [64, 256])
+def test_config1_200_steps(variant, block):
     c = synth.config1()
-    g, o = run_pair(c, 200, variant)
+    g, o = run_pair(c, 200, variant, block)
     err = rel_l2(g.state(), o.state())
     assert np.all(err <= TOL), err
     ma, mb = g.mass(), o.mass()
@@ -149,7 +150,7 @@ def test_config1_lake_at_rest():
     assert np.abs(u[0, 0] - 0.3).max() < 1e-12
 
 
-@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED])
+@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED])
 def test_shelf_wetdry_tide_run(variant):
     c = synth.config2(n=48)
     g, o = run_pair(c, 200, variant)
@@ -160,7 +161,7 @@ def test_shelf_wetdry_tide_run(variant):
     assert ma[1] == pytest.approx(mb[1], rel=1e-14)
 
 
-@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED])
+@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED])
 def test_storm_run(variant):
     c = synth.config3(n=40)
     g, o = run_pair(c, 100, variant)
@@ -169,7 +170,7 @@ def test_storm_run(variant):
     assert np.abs(g.state()[1]).max() > 1e-4  # the storm moved water
 
 
-@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED])
+@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED])
 def test_p2_run(variant):
     c = synth.config2(n=24, p=2)
     g, o = run_pair(c, 100, variant)
@@ -192,11 +193,12 @@ def test_mixed_precision_error_bound():
     assert abs(ma[1] - mb[1]) <= 1e-9 * mb[1]
 
 
-def test_bitwise_deterministic():
+@pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_TILED])
+def test_bitwise_deterministic(variant):
     c = synth.config2(n=40)
     outs = []
     for _ in range(2):
-        g = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, variant=VARIANT_SPLIT, block=128)
+        g = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, variant=variant, block=128)
         g.step(50)
         outs.append(g.state())
     assert np.array_equal(outs[0], outs[1])
