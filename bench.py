@@ -251,8 +251,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--profile", choices=["storm", "storm-mixed", "shelf", "shelf-mixed"],
-                    help="run 3 steps of one workload with the split variant, block 64 (for ncu)")
+    ap.add_argument("--profile", choices=["storm", "storm-mixed", "shelf", "shelf-mixed", "ensemble-small"],
+                    help="run 3 steps of one workload in a fixed launch configuration (for ncu)")
+    ap.add_argument("--variant", type=int, default=1, help="with --profile: 1 split, 2 fused, 3 tiled")
+    ap.add_argument("--block", type=int, default=64, help="with --profile: threads per block / tile size")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -267,13 +269,23 @@ def main():
     from paper_2508_21208_gb300.build import build_library
     build_library()
     torch.cuda.set_device(local)
+    if args.profile == "ensemble-small":
+        # 8 storms on the 199,712- and 399,618-element meshes (~2.4M elements per stage)
+        from paper_2508_21208_gb300 import Ensemble
+        meshes, bathys, members = synth.ensemble(members_per_mesh=4, mesh_n=(316, 447))
+        ens = Ensemble(meshes, bathys, members, block=args.block, mode=1, stream=torch.cuda.Stream())
+        ens.step(3)
+        ens.sync()
+        print(json.dumps({"profile": args.profile, "members": len(members), "steps": 3}))
+        return
     if args.profile:
         mixed = synth.FP32_MIXED if args.profile.endswith("mixed") else synth.FP64
         case = synth.config3(precision=mixed) if args.profile.startswith("storm") else synth.config2(precision=mixed)
-        m = make_model(case, torch.cuda.Stream(), variant=1, block=64)
+        m = make_model(case, torch.cuda.Stream(), variant=args.variant, block=args.block)
         m.step(3)
         m.sync()
-        print(json.dumps({"profile": args.profile, "elements": case.mesh.n_elems, "steps": 3}))
+        print(json.dumps({"profile": args.profile, "elements": case.mesh.n_elems, "steps": 3,
+                          "variant": args.variant, "block": args.block}))
         return
     dist = None
     if world > 1:
@@ -347,7 +359,8 @@ def extras(stream, flush, hbm):
     out = {}
     for key, case, form, p in (("fp32_mixed_p1", synth.config2(precision=synth.FP32_MIXED), "mixed", 1),
                                ("fp32_mixed_p2", synth.config2(p=2, precision=synth.FP32_MIXED), "mixed", 2),
-                               ("fp64_storm_3.2M", synth.config3(), "fp64", 1)):
+                               ("fp64_storm_3.2M", synth.config3(), "fp64", 1),
+                               ("fp32_mixed_storm_3.2M", synth.config3(precision=synth.FP32_MIXED), "mixed", 1)):
         m, ms, kt, (kps, variant, block) = run_form(case, 20, 3, stream, flush)
         rate = case.mesh.n_elems * 2 * 20 / (sum(ms) * 1e-3)
         name, avg_s, tot = dominant(kt)
@@ -369,6 +382,7 @@ def ensemble_form(stream, steps=10):
     meshes, bathys, members = synth.ensemble()
     ens = Ensemble(meshes, bathys, members, stream=stream)
     kps, mode, block = ens.graph_info()
+    tune = ens.tune_log()
     ens.step(3)
     ens.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -398,6 +412,7 @@ def ensemble_form(stream, steps=10):
     return {"value": units / (ms * 1e-3), "unit": UNIT, "members": len(members),
             "elements_per_stage": units // 2, "ms_per_step": ms, "mode": "persistent" if mode == 1 else "phased",
             "block": block, "gpu_launches_per_step": kps, "l2": "working set ~4 GB > L2, no flush",
+            "autotune_ms_per_step": tune,
             "fp64_sequential_ms_per_step": seq_ms, "fp64_single_ms_per_step_by_mesh": per_mesh,
             "speedup_vs_64_sequential_fp64": seq_ms / ms,
             "hbm_gbs_algorithmic": ALG_BYTES[("mixed", 1)] * units / (ms * 1e-3) / 1e9}

@@ -208,6 +208,12 @@ DGSWEM_API int dgswem_kernel_times(dgswem_ctx *ctx, float *ms, const char **name
 DGSWEM_API int dgswem_graph_info(dgswem_ctx *ctx, int32_t *kernels_per_step, int32_t *variant,
                       int32_t *block);
 
+/* The autotuner's measurements at attach: for each timed candidate its variant (single model:
+ * DGSWEM_VARIANT_*; ensemble: DGSWEM_ENSEMBLE_*), block / tile size and milliseconds per step.
+ * n_entries gets the count (0 when a fixed configuration was requested). */
+DGSWEM_API int dgswem_tune_log(dgswem_ctx *ctx, int32_t *variant, int32_t *block, float *ms_per_step,
+                               int32_t capacity, int32_t *n_entries);
+
 /* ---- batched ensemble (several scenarios, meshes of uneven size) ----
  * n members; member i uses meshes[i], bathy[i], params[i] and inits[i] (inits may be NULL).
  * Members that pass the same mesh and bathymetry pointers share one copy of the static mesh

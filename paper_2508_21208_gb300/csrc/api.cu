@@ -73,6 +73,11 @@ Phys make_phys(const dgswem_params &p) {
   ph.x0 = p.track_x0;
   ph.y0 = p.track_y0;
   ph.heading = p.track_heading;
+  ph.cos_h = std::cos(p.track_heading);
+  ph.sin_h = std::sin(p.track_heading);
+  ph.hB_rho_air = p.rho_air > 0 ? p.holland_b / p.rho_air : 0.0;
+  ph.rho_ratio = p.rho_water > 0 ? p.rho_air / p.rho_water : 0.0;
+  ph.inv_rho_w = p.rho_water > 0 ? 1.0 / p.rho_water : 0.0;
   ph.rho_air = p.rho_air;
   ph.rho_w = p.rho_water;
   ph.friction = p.friction;
@@ -220,7 +225,8 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
     double *uin = stage ? c->U1 : c->U0;
     double *out = stage ? c->U0 : c->U1;
     const Clock clk{c->step, c->t0, c->dt};
-    if (ph.hurricane) {
+    const bool inline_frc = ph.hurricane && c->mixed;  // mixed form: vortex evaluated per element vertex
+    if (ph.hurricane && !inline_frc) {
       mark(c, kname_forcing, names, &ev_i);
       launch_forcing(c->mixed, c->dm, ph, clk, stage, 0.0, c->frc, cfg);
     }
@@ -232,7 +238,8 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
     sa.wd = ph.wetdry ? c->wd : nullptr;
     sa.eflux = c->eflux;
     sa.emode = c->emode;
-    sa.frc = ph.hurricane ? c->frc : nullptr;
+    sa.frc = (ph.hurricane && !inline_frc) ? c->frc : nullptr;
+    sa.frc_inline = inline_frc ? 1 : 0;
     sa.clk = clk;
     sa.stage = stage;
     sa.err = c->err;
@@ -261,7 +268,7 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
 }
 
 static int kernels_in_step(const dgswem_ctx *c, int variant) {
-  int per_stage = 1 + (c->ph.hurricane ? 1 : 0) + ((variant == DGSWEM_VARIANT_SPLIT && c->dm.nint > 0) ? 1 : 0) +
+  int per_stage = 1 + ((c->ph.hurricane && !c->mixed) ? 1 : 0) + ((variant == DGSWEM_VARIANT_SPLIT && c->dm.nint > 0) ? 1 : 0) +
                   ((c->ph.limiter || c->ph.wetdry) ? 1 : 0);
   return 2 * per_stage + 1;
 }
@@ -642,7 +649,8 @@ int dgswem_eval_rhs(dgswem_ctx *c, double t, double *h_out) {
   if (c->sticky) return c->sticky;
   if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
   const LaunchCfg cfg{c->block, c->st};
-  if (c->ph.hurricane) launch_forcing(c->mixed, c->dm, c->ph, Clock{nullptr, 0, 0}, 0, t, c->frc, cfg);
+  const bool inline_frc = c->ph.hurricane && c->mixed;
+  if (c->ph.hurricane && !inline_frc) launch_forcing(c->mixed, c->dm, c->ph, Clock{nullptr, 0, 0}, 0, t, c->frc, cfg);
   StageArgs sa{};
   sa.uin = c->U0;
   sa.un = c->U0;
@@ -651,7 +659,8 @@ int dgswem_eval_rhs(dgswem_ctx *c, double t, double *h_out) {
   sa.wd = c->ph.wetdry ? c->wd : nullptr;
   sa.eflux = c->eflux;
   sa.emode = c->emode;
-  sa.frc = c->ph.hurricane ? c->frc : nullptr;
+  sa.frc = (c->ph.hurricane && !inline_frc) ? c->frc : nullptr;
+  sa.frc_inline = inline_frc ? 1 : 0;
   sa.clk = Clock{nullptr, 0.0, c->dt};
   sa.stage = 0;
   sa.err = c->err;
@@ -733,6 +742,18 @@ int dgswem_kernel_times(dgswem_ctx *c, float *ms, const char **names, int32_t ca
     if (names) names[i] = c->knames[i];
   }
   return ctx_cuda(c, cudaGetLastError(), "kernel times");
+}
+
+int dgswem_tune_log(dgswem_ctx *c, int32_t *variant, int32_t *block, float *ms, int32_t cap, int32_t *n) {
+  if (!c || !n) return DGSWEM_EINVAL;
+  const std::vector<TuneEntry> &log = c->ensemble ? ensemble_tune_log(c) : c->tune_log;
+  *n = (int32_t)log.size();
+  for (int32_t i = 0; i < *n && i < cap; ++i) {
+    if (variant) variant[i] = log[i].variant;
+    if (block) block[i] = log[i].block;
+    if (ms) ms[i] = log[i].ms_per_step;
+  }
+  return 0;
 }
 
 int dgswem_graph_info(dgswem_ctx *c, int32_t *kps, int32_t *variant, int32_t *block) {

@@ -89,3 +89,4 @@ int upload_mesh(dgswem_ctx *c, const dg::HostMesh &H, const dg::DevMesh &m, int 
 int ensemble_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream);
 void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names);
 void ensemble_release(dgswem_ctx *c);
+const std::vector<TuneEntry> &ensemble_tune_log(dgswem_ctx *c);

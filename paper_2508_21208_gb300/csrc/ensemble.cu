@@ -30,6 +30,8 @@ struct EnsMember {
 struct EnsMesh {
   HostMesh hm;
   DevMesh dm{};
+  DevTiles dt{};   // tile edge lists on the device (tile size dt.tile)
+  TileEdges ht;
   int *perm = nullptr, *iperm = nullptr;
   const dgswem_mesh *key_mesh = nullptr;
   const double *key_bathy = nullptr;
@@ -56,7 +58,16 @@ static void ens_layout(dgswem_ctx *c, char *base, size_t *bytes) {
   const int ND = c->ND;
   const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
   Carver k{base};
-  for (EnsMesh &m : E.meshes) carve_mesh(k, m.hm, c->P, c->mixed, m.dm, &m.perm, &m.iperm);
+  for (EnsMesh &m : E.meshes) {
+    carve_mesh(k, m.hm, c->P, c->mixed, m.dm, &m.perm, &m.iperm);
+    const int mt = max_tile_edges(m.hm);
+    m.dt.start = k.take<int>((m.hm.ne + 63) / 64 + 1);
+    m.dt.ea = k.take<int>(mt);
+    m.dt.eb = k.take<int>(mt);
+    m.dt.code = k.take<uint8_t>(mt);
+    m.dt.geo = k.take<char>(tsz * 3 * mt);
+    m.dt.hb = k.take<double>(2 * (size_t)mt);
+  }
   size_t stage = 0;
   for (EnsMember &mb : E.mem) {
     const HostMesh &H = E.meshes[mb.mesh].hm;
@@ -92,6 +103,7 @@ static void build_tiles(dgswem_ctx *c, int block) {
     const EnsMesh &M = E.meshes[mb.mesh];
     MemberDev &d = E.h_mem[i];
     d.m = M.dm;
+    d.tl = M.dt;
     d.ph = mb.ph;
     d.U0 = mb.U0;
     d.U1 = mb.U1;
@@ -107,7 +119,7 @@ static void build_tiles(dgswem_ctx *c, int block) {
   }
   for (size_t i = 0; i < E.mem.size(); ++i) {
     EnsMember &mb = E.mem[i];
-    if (!mb.ph.hurricane) continue;
+    if (!mb.ph.hurricane || c->mixed) continue;  // the mixed form evaluates the vortex per element vertex
     const EnsMesh &M = E.meshes[mb.mesh];
     E.h_mem[i].ntile0 = (int)E.h_ntile.size();
     const int nt = (M.hm.nn + block - 1) / block;
@@ -193,8 +205,37 @@ void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names) {
   c->kernels_per_step = E.persistent ? 1 : 2 * ((E.n_ntile > 0) + 1 + E.any_limwd) + 1;
 }
 
+static int upload_mesh_tiles(dgswem_ctx *c, EnsMesh &M, int tile) {
+  if (M.dt.tile == tile) return 0;
+  build_tile_edges(M.hm, tile, M.ht);
+  if (M.ht.n > max_tile_edges(M.hm)) return ctx_fail(c, DGSWEM_EINVAL, "tile list larger than its buffer");
+  std::vector<char> geo(M.ht.geo.size() * (c->mixed ? 4 : 8));
+  for (size_t i = 0; i < M.ht.geo.size(); ++i) {
+    if (c->mixed) reinterpret_cast<float *>(geo.data())[i] = (float)M.ht.geo[i];
+    else reinterpret_cast<double *>(geo.data())[i] = M.ht.geo[i];
+  }
+  cudaStream_t s = c->st;
+  int r = 0;
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(M.dt.start), M.ht.start.data(), M.ht.start.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, s), "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(M.dt.ea), M.ht.ea.data(), M.ht.n * sizeof(int), cudaMemcpyHostToDevice, s), "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(M.dt.eb), M.ht.eb.data(), M.ht.n * sizeof(int), cudaMemcpyHostToDevice, s), "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<uint8_t *>(M.dt.code), M.ht.code.data(), M.ht.n, cudaMemcpyHostToDevice, s), "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(M.dt.geo), geo.data(), geo.size(), cudaMemcpyHostToDevice, s), "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<double *>(M.dt.hb), M.ht.hb.data(), M.ht.hb.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice, s), "tiles");
+  if (r) return c->sticky;
+  if (int e = ctx_cuda(c, cudaStreamSynchronize(s), "tiles sync")) return e;
+  M.dt.tile = tile;
+  M.dt.ntiles = M.ht.ntiles;
+  M.dt.n = M.ht.n;
+  return 0;
+}
+
 static int configure(dgswem_ctx *c, bool persistent, int block) {
   EnsembleState &E = *c->ens;
+  for (EnsMesh &M : E.meshes)
+    if (int r = upload_mesh_tiles(c, M, block)) return r;
   build_tiles(c, block);
   E.persistent = persistent;
   E.block = block;
@@ -209,6 +250,7 @@ int ensemble_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream
   EnsembleState &E = *c->ens;
   size_t sz = 0;
   ens_layout(c, c->ws, &sz);
+  for (EnsMesh &m : E.meshes) m.dt.tile = 0;
   c->host_keep.clear();
   for (EnsMesh &m : E.meshes)
     if (int r = upload_mesh(c, m.hm, m.dm, m.perm, m.iperm)) return r;
@@ -278,6 +320,8 @@ int ensemble_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream
   if (int r = init_states(c)) return r;
   return read_error_word(c);
 }
+
+const std::vector<TuneEntry> &ensemble_tune_log(dgswem_ctx *c) { return c->ens->tune; }
 
 void ensemble_release(dgswem_ctx *c) {
   delete c->ens;

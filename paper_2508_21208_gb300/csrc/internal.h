@@ -77,6 +77,8 @@ struct Phys {
   double g, sqrt_g, h0, cf, gn2, fcor;
   double tide_amp, tide_omega, tide_phase;
   double pc, pn, rmax, hB, vt, x0, y0, heading, flat, rho_air, rho_w;
+  double cos_h, sin_h;     // heading direction of the storm track
+  double hB_rho_air, rho_ratio, inv_rho_w;  // B / rho_air, rho_air / rho_w, 1 / rho_w
   int friction, wetdry, limiter, hurricane;
 };
 
@@ -99,15 +101,6 @@ struct DevMesh {
   const double *nodexy;    // [2][nn]
 };
 
-struct DevTiles {
-  int tile, ntiles;
-  const int *start;        // [ntiles + 1]
-  const int *ea, *eb;      // [n]
-  const uint8_t *code;     // [n]
-  const void *geo;         // T [3][n]
-  const double *hb;        // [2][n]
-  int n;
-};
 
 struct Clock {
   const long long *step;   // device counter of completed steps
@@ -123,15 +116,27 @@ struct StageArgs {
   void *eflux;             // T [3][NQE][nint] weighted interior-edge fluxes (split variant)
   uint8_t *emode;          // [nint] 1 = the edge flux in eflux applies, 0 = both sides see a wall
   const void *frc;         // T [3][nn] nodal forcing at the stage time, or nullptr
+  int frc_inline;          // 1: evaluate the forcing at the element's vertices (mixed form)
   Clock clk;
   int stage;
   int *err;
   double tide_t;           // stage time when clk.step is null (single operator calls)
 };
 
+struct DevTiles {
+  int tile, ntiles;
+  const int *start;        // [ntiles + 1]
+  const int *ea, *eb;      // [n]
+  const uint8_t *code;     // [n]
+  const void *geo;         // T [3][n]
+  const double *hb;        // [2][n]
+  int n;
+};
+
 // One ensemble member (scenario) as the ensemble kernels see it.
 struct MemberDev {
   DevMesh m;               // the member's mesh statics (shared with members on the same mesh)
+  DevTiles tl;             // the mesh's tile edge lists for the ensemble's tile size
   Phys ph;
   double *U0, *U1, *mean;  // its own state
   uint8_t *wd;

@@ -57,6 +57,14 @@ template <typename T>
 __device__ __forceinline__ double to_d(T x) { return (double)x; }
 template <>
 __device__ __forceinline__ double to_d<float>(float x) { return f2d(x); }
+// x / 2, exactly, by lowering the exponent field on the integer pipe (zero stays zero; numbers
+// too small for that fall back to a multiply).
+__device__ __forceinline__ double half_exact(double x) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (ex > 1 && ex < 0x7ff) return __hiloint2double(hi - 0x00100000, __double2loint(x));
+  return 0.5 * x;
+}
 // finiteness from the exponent bits (no floating-point compare)
 __device__ __forceinline__ bool finite_bits(double x) {
   return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
@@ -161,15 +169,18 @@ __device__ __forceinline__ void load_modes(const double *u, int ne, int e, T w[3
 // counter-clockwise plus half the translation velocity; Garratt (1977) drag
 // C_d = min(0.75 + 0.067 |U|, 3.5) 1e-3.  Output per node: tau/rho_w (x, y) and the pressure
 // anomaly (p - pn)/rho_w (only its gradient enters the momentum source).
+// Storm centre at time t (double: coordinates are O(1e5) m).
+__device__ __forceinline__ void storm_center(const Phys &ph, double t, double &cx, double &cy) {
+  cx = ph.x0 + ph.vt * ph.cos_h * t;
+  cy = ph.y0 + ph.vt * ph.sin_h * t;
+}
+
+// Forcing at a point (dx, dy) from the storm centre: tau/rho_w and (p - pn)/rho_w.
 template <typename T>
-__device__ __forceinline__ void forcing_body(const double *nodexy, int nn, const Phys &ph, double t, T *frc,
-                                             int n) {
-  const double ch = cos(ph.heading), sh = sin(ph.heading);
-  const T dx = (T)(nodexy[n] - (ph.x0 + ph.vt * ch * t));
-  const T dy = (T)(nodexy[nn + n] - (ph.y0 + ph.vt * sh * t));
+__device__ __forceinline__ void vortex_at(const Phys &ph, T dx, T dy, T &tx_out, T &ty_out, T &pa_out) {
   const T r = sqrt(dx * dx + dy * dy);
   const T dp = (T)(ph.pn - ph.pc);
-  const T tx = T(0.5) * (T)(ph.vt * ch), ty = T(0.5) * (T)(ph.vt * sh);
+  const T tx = T(0.5) * (T)(ph.vt * ph.cos_h), ty = T(0.5) * (T)(ph.vt * ph.sin_h);
   T pa, ux, uy;
   if (r < T(1)) {
     pa = -dp;
@@ -179,17 +190,68 @@ __device__ __forceinline__ void forcing_body(const double *nodexy, int nn, const
     const T A = pow((T)ph.rmax / r, (T)ph.hB), E = exp(-A);
     pa = -dp + dp * E;
     const T hf = T(0.5) * r * (T)ph.flat;
-    const T V = sqrt((T)ph.hB / (T)ph.rho_air * dp * A * E + hf * hf) - hf;
+    const T V = sqrt((T)ph.hB_rho_air * dp * A * E + hf * hf) - hf;
     ux = T(0.9) * V * (-dy / r) + tx;
     uy = T(0.9) * V * (dx / r) + ty;
   }
   const T U = sqrt(ux * ux + uy * uy);
   T cd = T(0.75) + T(0.067) * U;
   cd = (cd > T(3.5) ? T(3.5) : cd) * T(1e-3);
-  const T k = (T)(ph.rho_air / ph.rho_w) * cd * U;
-  frc[n] = k * ux;
-  frc[nn + n] = k * uy;
-  frc[2 * nn + n] = pa / (T)ph.rho_w;
+  const T k = (T)ph.rho_ratio * cd * U;
+  tx_out = k * ux;
+  ty_out = k * uy;
+  pa_out = pa / (T)ph.rho_w;
+}
+
+// The mixed form's vortex: one reciprocal square root for 1/r, the hardware log2/exp2/exp
+// approximations for (Rmax/r)^B and exp(-A) (a few float ulp) and multiplications by host-computed
+// constants.  Out of line, so that every kernel that evaluates it rounds identically.
+static __device__ __noinline__ void vortex_at_f(const Phys &ph, float dx, float dy, float *out) {
+  const float r2 = dx * dx + dy * dy;
+  const float dp = (float)(ph.pn - ph.pc);
+  const float tx = 0.5f * (float)(ph.vt * ph.cos_h), ty = 0.5f * (float)(ph.vt * ph.sin_h);
+  float pa, ux, uy;
+  if (r2 < 1.f) {
+    pa = -dp;
+    ux = tx;
+    uy = ty;
+  } else {
+    const float ir = rsqrtf(r2), r = r2 * ir;
+    const float A = exp2f((float)ph.hB * __log2f((float)ph.rmax * ir)), E = __expf(-A);
+    pa = -dp + dp * E;
+    const float hf = 0.5f * r * (float)ph.flat;
+    const float V = sqrtf((float)ph.hB_rho_air * dp * A * E + hf * hf) - hf;
+    ux = 0.9f * V * (-dy * ir) + tx;
+    uy = 0.9f * V * (dx * ir) + ty;
+  }
+  const float U = sqrtf(ux * ux + uy * uy);
+  float cd = 0.75f + 0.067f * U;
+  cd = (cd > 3.5f ? 3.5f : cd) * 1e-3f;
+  const float k = (float)ph.rho_ratio * cd * U;
+  out[0] = k * ux;
+  out[1] = k * uy;
+  out[2] = pa * (float)ph.inv_rho_w;
+}
+template <>
+__device__ __forceinline__ void vortex_at<float>(const Phys &ph, float dx, float dy, float &tx_out, float &ty_out,
+                                                 float &pa_out) {
+  float o[3];
+  vortex_at_f(ph, dx, dy, o);
+  tx_out = o[0];
+  ty_out = o[1];
+  pa_out = o[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void forcing_body(const double *nodexy, int nn, const Phys &ph, double t, T *frc,
+                                             int n) {
+  T a, b, c;
+  double cx, cy;
+  storm_center(ph, t, cx, cy);
+  vortex_at<T>(ph, from_d<T>(nodexy[n] - cx), from_d<T>(nodexy[nn + n] - cy), a, b, c);
+  frc[n] = a;
+  frc[nn + n] = b;
+  frc[2 * nn + n] = c;
 }
 
 template <typename T>
@@ -279,9 +341,8 @@ struct ElemCtx {
 };
 
 template <int P, typename T>
-__device__ __forceinline__ void elem_load(const DevMesh &m, const double *u, int e, ElemCtx<P, T> &c) {
+__device__ __forceinline__ void elem_load_geom(const DevMesh &m, int e, ElemCtx<P, T> &c) {
   const int ne = m.ne;
-  load_modes<P, T>(u, ne, e, c.w);
   const T *geo = (const T *)m.geo;
   c.rx = geo[GEO_RX * (size_t)ne + e];
   c.ry = geo[GEO_RY * (size_t)ne + e];
@@ -292,6 +353,12 @@ __device__ __forceinline__ void elem_load(const DevMesh &m, const double *u, int
   c.hbd[1] = m.hbv[ne + e];
   c.hbd[2] = m.hbv[2 * (size_t)ne + e];
   for (int a = 0; a < 3; ++a) c.hb[a] = from_d<T>(c.hbd[a]);
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void elem_load(const DevMesh &m, const double *u, int e, ElemCtx<P, T> &c) {
+  load_modes<P, T>(u, m.ne, e, c.w);
+  elem_load_geom<P, T>(m, e, c);
 }
 
 // Area integrals (Alg. 1): advective + pressure flux and friction, r_k set (not accumulated).
@@ -396,13 +463,24 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
       src1[k] = g * hbx * w[0][k] + fc * w[2][k];
       src2[k] = g * hby * w[0][k] - fc * w[1][k];
     }
-    if (s.frc) {
-      const T *F = (const T *)s.frc;
+    if (s.frc || s.frc_inline) {
       const int nn = m.nn;
       const int n0 = m.vnode[e], n1 = m.vnode[ne + e], n2 = m.vnode[2 * (size_t)ne + e];
-      const T t0 = F[n0], t1 = F[n1], t2 = F[n2];
-      const T u0 = F[nn + n0], u1 = F[nn + n1], u2 = F[nn + n2];
-      const T p0 = F[2 * nn + n0], p1 = F[2 * nn + n1], p2 = F[2 * nn + n2];
+      T t0, t1, t2, u0, u1, u2, p0, p1, p2;
+      if (s.frc_inline) {
+        // the centre once per element; vertex offsets in T (O(1e5) m coordinates, float ulp ~1 cm)
+        double cxd, cyd;
+        storm_center(ph, stage_time(s.clk, s.stage, s.tide_t), cxd, cyd);
+        const T cx = from_d<T>(cxd), cy = from_d<T>(cyd);
+        vortex_at<T>(ph, from_d<T>(m.nodexy[n0]) - cx, from_d<T>(m.nodexy[nn + n0]) - cy, t0, u0, p0);
+        vortex_at<T>(ph, from_d<T>(m.nodexy[n1]) - cx, from_d<T>(m.nodexy[nn + n1]) - cy, t1, u1, p1);
+        vortex_at<T>(ph, from_d<T>(m.nodexy[n2]) - cx, from_d<T>(m.nodexy[nn + n2]) - cy, t2, u2, p2);
+      } else {
+        const T *F = (const T *)s.frc;
+        t0 = F[n0]; t1 = F[n1]; t2 = F[n2];
+        u0 = F[nn + n0]; u1 = F[nn + n1]; u2 = F[nn + n2];
+        p0 = F[2 * nn + n0]; p1 = F[2 * nn + n1]; p2 = F[2 * nn + n2];
+      }
       const T pax = T(0.5) * (rx * (p1 - p0) + sx * (p2 - p0));
       const T pay = T(0.5) * (ry * (p1 - p0) + sy * (p2 - p0));
       // Dubiner linear modes of the interpolant through vertex values (a0, a1, a2)
@@ -447,7 +525,8 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
       } else if (s.stage == 0) {
         out = s.uin[ix] + dt * Ld;
       } else {
-        out = 0.5 * s.un[ix] + 0.5 * (s.uin[ix] + dt * Ld);
+        // u/2 + (u1 + dt L)/2 == (u + (u1 + dt L)) / 2 exactly (halving commutes with rounding)
+        out = half_exact(s.un[ix] + (s.uin[ix] + dt * Ld));
       }
       bad |= !finite_bits(out);
       s.uout[ix] = out;
@@ -592,24 +671,26 @@ __global__ void __launch_bounds__(256)
 // Shared memory: double state [3*ND][tile], float/double flux slots [3][NQE][3][tile], flags.
 template <int P, typename T>
 __host__ __device__ constexpr size_t tile_smem_bytes(int tile) {
-  return sizeof(double) * 3 * nd_of(P) * tile + sizeof(T) * 9 * nqe_of(P) * tile + tile;
+  return sizeof(T) * 3 * nd_of(P) * tile + sizeof(T) * 9 * nqe_of(P) * tile + tile;
 }
 
+// Modes of element e: from the tile's shared-memory copy (already in T) or, for a neighbour in
+// another tile, from global memory.
 template <int P, typename T>
-__device__ __forceinline__ void tile_modes(const double *s_ud, int B, const double *u, int ne, int e, bool local,
+__device__ __forceinline__ void tile_modes(const T *s_u, int B, const double *u, int ne, int e, bool local,
                                            int li, T w[3][nd_of(P)]) {
 #pragma unroll
   for (int v = 0; v < 3; ++v)
 #pragma unroll
     for (int k = 0; k < nd_of(P); ++k) {
       const int row = v * nd_of(P) + k;
-      w[v][k] = from_d<T>(local ? s_ud[row * B + li] : __ldg(&u[(size_t)row * ne + e]));
+      w[v][k] = local ? s_u[row * B + li] : from_d<T>(__ldg(&u[(size_t)row * ne + e]));
     }
 }
 
 template <int P, typename T>
 __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, const StageArgs &s, const Phys &ph,
-                                          const int x, const int e0, const double *s_ud, T *s_slot,
+                                          const int x, const int e0, const T *s_ud, T *s_slot,
                                           const uint8_t *s_wd, const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
   constexpr int ND = nd_of(P), NQE = nqe_of(P);
   const Tab<T> &tb = ctab<T>(P);
@@ -701,45 +782,59 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
   }
 }
 
+// One tile: stage, edges, barrier, elements.  Called with the whole block (uses __syncthreads).
 template <int P, typename T>
-__global__ void __launch_bounds__(256)
-    k_tile(const DevMesh m, const DevTiles tl, const StageArgs s, const Phys ph, const int write_rhs) {
+__device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, const StageArgs &s, const Phys &ph,
+                                          const int write_rhs, const int tile, unsigned char *smem_raw,
+                                          const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
   constexpr int ND = nd_of(P), NQE = nqe_of(P);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T s_phe[3][NQE][ND];
   const int B = tl.tile, ne = m.ne;
-  double *s_ud = reinterpret_cast<double *>(smem_raw);
-  T *s_slot = reinterpret_cast<T *>(s_ud + (size_t)3 * ND * B);
+  T *s_ud = reinterpret_cast<T *>(smem_raw);
+  T *s_slot = s_ud + (size_t)3 * ND * B;
   uint8_t *s_wd = reinterpret_cast<uint8_t *>(s_slot + (size_t)9 * NQE * B);
-  load_phe<P, T>(s_phe);
-  const int e0 = blockIdx.x * B, i = threadIdx.x;
+  const int e0 = tile * B, i = threadIdx.x;
   const int nloc = min(B, ne - e0);
   if (i < nloc) {
 #pragma unroll
-    for (int r = 0; r < 3 * ND; ++r) s_ud[r * B + i] = __ldg(&s.uin[(size_t)r * ne + e0 + i]);
+    for (int r = 0; r < 3 * ND; ++r) s_ud[r * B + i] = from_d<T>(__ldg(&s.uin[(size_t)r * ne + e0 + i]));
     s_wd[i] = s.wd ? s.wd[e0 + i] : 0;
   }
   __syncthreads();
-  const int beg = tl.start[blockIdx.x], end = tl.start[blockIdx.x + 1];
+  const int beg = tl.start[tile], end = tl.start[tile + 1];
   for (int x = beg + i; x < end; x += B) tile_edge<P, T>(m, tl, s, ph, x, e0, s_ud, s_slot, s_wd, s_phe);
   __syncthreads();
-  if (i >= nloc) return;
-  const int e = e0 + i;
-  ElemCtx<P, T> c;
-  elem_load<P, T>(m, s.uin, e, c);
-  T r[3][ND];
-  elem_area<P, T>(c, ph, r);
+  if (i < nloc) {
+    const int e = e0 + i;
+    ElemCtx<P, T> c;
+    elem_load_geom<P, T>(m, e, c);
 #pragma unroll
-  for (int l = 0; l < 3; ++l)
+    for (int v = 0; v < 3; ++v)
 #pragma unroll
-    for (int q = 0; q < NQE; ++q)
+      for (int k = 0; k < ND; ++k) c.w[v][k] = s_ud[(v * ND + k) * B + i];
+    T r[3][ND];
+    elem_area<P, T>(c, ph, r);
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        const T f = s_slot[(size_t)((l * NQE + q) * 3 + v) * B + i];
+    for (int l = 0; l < 3; ++l)
 #pragma unroll
-        for (int k = 0; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
-      }
-  elem_finish<P, T>(m, s, ph, write_rhs, e, c, r);
+      for (int q = 0; q < NQE; ++q)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const T f = s_slot[(size_t)((l * NQE + q) * 3 + v) * B + i];
+#pragma unroll
+          for (int k = 0; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
+        }
+    elem_finish<P, T>(m, s, ph, write_rhs, e, c, r);
+  }
+  __syncthreads();  // the shared-memory tile is reused by the block's next tile
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(256)
+    k_tile(const DevMesh m, const DevTiles tl, const StageArgs s, const Phys ph, const int write_rhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
+  load_phe<P, T>(s_phe);
+  tile_body<P, T>(m, tl, s, ph, write_rhs, blockIdx.x, smem_raw, s_phe);
 }
 
 // ------------------------------------------------------------------------ SLOPELIM + WETDRY
@@ -762,6 +857,36 @@ constexpr double WD_TOL = 1e-10;  // m: depths within this of h0 count as "at h0
 // <= h0 (dry), else lift vertices below h0 to h0 and rescale the others' excess (mean kept);
 // momentum removed where dry, or partially wet with the mean surface below the highest bed of the
 // vertices at h0; at p = 2 limited or non-wet elements drop their quadratic modes.
+// Rare path of the limiter, kept out of line so that its divisions are not executed
+// speculatively for every element: rescale the limited midpoint deviations so that they sum to
+// zero (theta+/- rule) and rebuild the linear modes from the midpoints of local edges 0 and 1.
+template <int P, typename T>
+__device__ __noinline__ void limiter_rebuild(const T d[3], double *u1, double *u2) {
+  const Tab<T> &tb = ctab<T>(P);
+  T pos = 0, neg = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    pos += d[i] > T(0) ? d[i] : T(0);
+    neg += d[i] < T(0) ? -d[i] : T(0);
+  }
+  T tp = T(0), tm = T(0);
+  if (pos > T(0) && neg > T(0)) {
+    if (neg <= pos) {
+      tp = neg / pos;
+      tm = T(1);
+    } else {
+      tp = T(1);
+      tm = pos / neg;
+    }
+  }
+  T dh[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dh[i] = tp * (d[i] > T(0) ? d[i] : T(0)) - tm * (d[i] < T(0) ? -d[i] : T(0));
+  const T det = tb.phm[0][1] * tb.phm[1][2] - tb.phm[0][2] * tb.phm[1][1];
+  *u1 = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) / det);
+  *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) / det);
+}
+
 template <int P, typename T>
 __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const double *mean, uint8_t *wd,
                                            const Phys &ph, int *err, int do_lim, int do_wd, const int e) {
@@ -778,12 +903,47 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
     bool any = false;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      const T u0 = from_d<T>(u[(size_t)(v * ND) * ne + e]);
-      const T u1 = from_d<T>(u[(size_t)(v * ND + 1) * ne + e]);
-      const T u2 = from_d<T>(u[(size_t)(v * ND + 2) * ne + e]);
+      const double d0 = u[(size_t)(v * ND) * ne + e];
+      const double d1 = u[(size_t)(v * ND + 1) * ne + e];
+      const double d2 = u[(size_t)(v * ND + 2) * ne + e];
+      double db3[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) db3[j] = nb[j] >= 0 ? mean[(size_t)v * ne + nb[j]] : d0;
+      if constexpr (sizeof(T) == sizeof(double)) {
+        // Filtered predicate (after Shewchuk's floating-point filters): a float evaluation with an
+        // error margin well above its rounding proves, when it can, that minmod returns the midpoint
+        // deviation at every edge, i.e. the limiter leaves this variable untouched; only the
+        // undecided cases run the exact double test below.  Zero slopes are untouched exactly.
+        if (((__double_as_longlong(d1) | __double_as_longlong(d2)) << 1) == 0) continue;  // both +-0
+        const float f0 = d2f(d0), f1 = d2f(d1), f2 = d2f(d2);
+        const Tab<float> &tf = ctab<float>(P);
+        bool sure = true;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float p1 = tf.phm[i][1], p2 = tf.phm[i][2];
+          const float ut = f1 * p1 + f2 * p2;
+          const float eu = 1e-6f * (fabsf(f1 * p1) + fabsf(f2 * p2));
+          const unsigned c = (code >> (4 * i)) & 15u;
+          const int j1 = c & 3, j2 = c >> 2;
+          float db = 0.f, ed = 0.f;
+          if (j1 != 3) {
+            const float a1 = d2f(A[(size_t)(2 * i) * ne + e]), a2 = d2f(A[(size_t)(2 * i + 1) * ne + e]);
+            const float b1 = d2f(db3[j1]), b2 = d2f(db3[j2]);
+            db = 1.5f * (a1 * (b1 - f0) + a2 * (b2 - f0));
+            ed = 1e-6f * 1.5f * (fabsf(a1) * (fabsf(b1) + fabsf(f0)) + fabsf(a2) * (fabsf(b2) + fabsf(f0))) + 1e-30f;
+          }
+          const bool ok = (fabsf(ut) > eu) && (fabsf(db) > ed) && ((ut > 0.f) == (db > 0.f)) &&
+                          (fabsf(ut) + eu < fabsf(db) - ed);
+          sure = sure && ok;
+        }
+        if (sure) continue;
+      }
+      const T u0 = from_d<T>(d0);
+      const T u1 = from_d<T>(d1);
+      const T u2 = from_d<T>(d2);
       T ub[3];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) ub[j] = nb[j] >= 0 ? from_d<T>(mean[(size_t)v * ne + nb[j]]) : u0;
+      for (int j = 0; j < 3; ++j) ub[j] = from_d<T>(db3[j]);
       T d[3];
       bool act = false;
 #pragma unroll
@@ -798,21 +958,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
       }
       if (!act) continue;
       any = true;
-      T pos = 0, neg = 0;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        pos += d[i] > T(0) ? d[i] : T(0);
-        neg += d[i] < T(0) ? -d[i] : T(0);
-      }
-      const T tp = pos > T(0) ? (neg / pos < T(1) ? neg / pos : T(1)) : T(0);
-      const T tm = neg > T(0) ? (pos / neg < T(1) ? pos / neg : T(1)) : T(0);
-      T dh[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) dh[i] = tp * (d[i] > T(0) ? d[i] : T(0)) - tm * (d[i] < T(0) ? -d[i] : T(0));
-      // linear function with deviations dh at the midpoints of local edges 0 and 1
-      const T det = tb.phm[0][1] * tb.phm[1][2] - tb.phm[0][2] * tb.phm[1][1];
-      u[(size_t)(v * ND + 1) * ne + e] = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) / det);
-      u[(size_t)(v * ND + 2) * ne + e] = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) / det);
+      limiter_rebuild<P, T>(d, u + (size_t)(v * ND + 1) * ne + e, u + (size_t)(v * ND + 2) * ne + e);
     }
     if constexpr (P == 2) {
       if (any)
@@ -825,9 +971,10 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
     const double h0 = ph.h0;
     const double hbv[3] = {m.hbv[e], m.hbv[ne + e], m.hbv[2 * (size_t)ne + e]};
     const double z0 = u[e], z1 = u[(size_t)ne + e], z2 = u[2 * (size_t)ne + e];
-    if constexpr (sizeof(T) == sizeof(float)) {
-      // Mixed form: a float evaluation decides the clearly wet elements (every vertex depth
-      // exceeds h0 by more than the float rounding of its terms); only the rest are tested in double.
+    {
+      // Filtered predicate: a float evaluation decides the clearly wet elements (every vertex depth
+      // exceeds h0 by far more than the float rounding of its terms), for which the double test
+      // below would change nothing; only the rest are tested in double.
       const float fz0 = d2f(z0), fz1 = d2f(z1), fz2 = d2f(z2);
       const float fh0 = d2f(hbv[0]), fh1 = d2f(hbv[1]), fh2 = d2f(hbv[2]);
       const float mag = fabsf(fz0) + fabsf(fz1) + 2.f * fabsf(fz2) + fmaxf(fabsf(fh0), fmaxf(fabsf(fh1), fabsf(fh2)));
@@ -943,7 +1090,8 @@ __device__ __forceinline__ bool grid_barrier(const EnsArgs &a, bool skip) {
   return (*(volatile int *)a.err & ERR_TIMEOUT) == 0;
 }
 
-// Stage arguments of member md (fused element variant: no edge scratch).
+// Stage arguments of member md (no edge scratch; the mixed form evaluates forcing inline).
+template <typename T>
 __device__ __forceinline__ StageArgs member_stage(const MemberDev &md, const EnsArgs &a, int stage) {
   StageArgs sa;
   sa.uin = stage ? md.U1 : md.U0;
@@ -953,7 +1101,9 @@ __device__ __forceinline__ StageArgs member_stage(const MemberDev &md, const Ens
   sa.wd = md.ph.wetdry ? md.wd : nullptr;
   sa.eflux = nullptr;
   sa.emode = nullptr;
-  sa.frc = md.ph.hurricane ? md.frc : nullptr;
+  const bool inl = md.ph.hurricane && sizeof(T) == sizeof(float);
+  sa.frc = (md.ph.hurricane && !inl) ? md.frc : nullptr;
+  sa.frc_inline = inl ? 1 : 0;
   sa.clk = Clock{a.step, md.t0, md.dt};
   sa.stage = stage;
   sa.err = a.err;
@@ -972,7 +1122,16 @@ __device__ __forceinline__ void load_member(MemberDev *dst, const MemberDev *src
 
 template <int P, typename T>
 __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage, int t_begin, int t_step,
-                                          MemberDev *sd, const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
+                                          MemberDev *sd, const T (*s_phe)[nqe_of(P)][nd_of(P)],
+                                          unsigned char *smem_raw) {
+  if (phase == 1) {  // element update, one shared-memory tile per work item
+    for (int t = t_begin; t < a.n_etile; t += t_step) {
+      load_member(sd, &a.mem[a.etile[t]]);
+      const StageArgs sa = member_stage<T>(*sd, a, stage);
+      tile_body<P, T>(sd->m, sd->tl, sa, sd->ph, 0, t - sd->etile0, smem_raw, s_phe);
+    }
+    return;
+  }
   if (phase == 0) {  // WIND at the nodes of members with a hurricane
     for (int t = t_begin; t < a.n_ntile; t += t_step) {
       load_member(sd, &a.mem[a.ntile[t]]);
@@ -987,8 +1146,7 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
       const int e = (t - sd->etile0) * blockDim.x + threadIdx.x;
       if (e >= sd->m.ne) continue;
       if (phase == 1) {
-        const StageArgs sa = member_stage(*sd, a, stage);
-        element_body<P, T, false>(sd->m, sa, sd->ph, 0, e, s_phe);
+        continue;  // handled by the tiled loop below
       } else if (sd->ph.limiter || sd->ph.wetdry) {
         limwd_body<P, T>(sd->m, stage ? sd->U0 : sd->U1, sd->mean, sd->wd, sd->ph, a.err, sd->ph.limiter,
                          sd->ph.wetdry, e);
@@ -1001,6 +1159,7 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
 // limiter/wet-dry over the flat tile lists, separated by bounded grid barriers.
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_ens_persistent(const EnsArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   __shared__ MemberDev sd;
   load_phe<P, T>(s_phe);
@@ -1009,13 +1168,13 @@ __global__ void __launch_bounds__(256) k_ens_persistent(const EnsArgs a) {
   const bool skip = a.fault && blockIdx.x == gridDim.x - 1;
   for (int stage = 0; stage < 2; ++stage) {
     if (a.n_ntile > 0) {
-      ens_phase<P, T>(a, 0, stage, blockIdx.x, gridDim.x, &sd, s_phe);
+      ens_phase<P, T>(a, 0, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
       if (!grid_barrier(a, skip)) return;
     }
-    ens_phase<P, T>(a, 1, stage, blockIdx.x, gridDim.x, &sd, s_phe);
+    ens_phase<P, T>(a, 1, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
     if (!grid_barrier(a, skip)) return;
     if (a.any_limwd) {
-      ens_phase<P, T>(a, 2, stage, blockIdx.x, gridDim.x, &sd, s_phe);
+      ens_phase<P, T>(a, 2, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
       if (stage == 0 && !grid_barrier(a, skip)) return;
     }
   }
@@ -1025,11 +1184,12 @@ __global__ void __launch_bounds__(256) k_ens_persistent(const EnsArgs a) {
 // The same phases as separate launches (one tile per block); the stream orders them.
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_ens_phase(const EnsArgs a, int phase, int stage) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   __shared__ MemberDev sd;
   load_phe<P, T>(s_phe);
   __syncthreads();
-  ens_phase<P, T>(a, phase, stage, blockIdx.x, gridDim.x, &sd, s_phe);
+  ens_phase<P, T>(a, phase, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
 }
 
 template <typename T>
@@ -1039,6 +1199,7 @@ cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int bloc
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
     cfg.stream = s;
+    cfg.dynamicSmemBytes = p == 1 ? tile_smem_bytes<1, T>(block) : tile_smem_bytes<2, T>(block);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
@@ -1047,16 +1208,17 @@ cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int bloc
     return p == 1 ? cudaLaunchKernelEx(&cfg, k_ens_persistent<1, T>, a)
                   : cudaLaunchKernelEx(&cfg, k_ens_persistent<2, T>, a);
   }
+  const size_t sm = p == 1 ? tile_smem_bytes<1, T>(block) : tile_smem_bytes<2, T>(block);
   for (int stage = 0; stage < 2; ++stage) {
     if (a.n_ntile > 0) {
-      if (p == 1) k_ens_phase<1, T><<<a.n_ntile, block, 0, s>>>(a, 0, stage);
-      else k_ens_phase<2, T><<<a.n_ntile, block, 0, s>>>(a, 0, stage);
+      if (p == 1) k_ens_phase<1, T><<<a.n_ntile, block, sm, s>>>(a, 0, stage);
+      else k_ens_phase<2, T><<<a.n_ntile, block, sm, s>>>(a, 0, stage);
     }
-    if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, 0, s>>>(a, 1, stage);
-    else k_ens_phase<2, T><<<a.n_etile, block, 0, s>>>(a, 1, stage);
+    if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, sm, s>>>(a, 1, stage);
+    else k_ens_phase<2, T><<<a.n_etile, block, sm, s>>>(a, 1, stage);
     if (a.any_limwd) {
-      if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, 0, s>>>(a, 2, stage);
-      else k_ens_phase<2, T><<<a.n_etile, block, 0, s>>>(a, 2, stage);
+      if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, sm, s>>>(a, 2, stage);
+      else k_ens_phase<2, T><<<a.n_etile, block, sm, s>>>(a, 2, stage);
     }
   }
   return cudaGetLastError();
@@ -1066,9 +1228,9 @@ template <typename T>
 int ensemble_blocks_per_sm_t(int p, int block) {
   int n = 0;
   if (p == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<1, T>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<1, T>, block, tile_smem_bytes<1, T>(block));
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<2, T>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<2, T>, block, tile_smem_bytes<2, T>(block));
   return n;
 }
 
@@ -1137,6 +1299,12 @@ void prepare_tile_t() {
   // allow the largest tile's dynamic shared memory (p = 2, 256 elements)
   cudaFuncSetAttribute(k_tile<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256));
   cudaFuncSetAttribute(k_tile<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256));
+  cudaFuncSetAttribute(k_ens_persistent<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tile_smem_bytes<1, T>(256));
+  cudaFuncSetAttribute(k_ens_persistent<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tile_smem_bytes<2, T>(256));
+  cudaFuncSetAttribute(k_ens_phase<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256));
+  cudaFuncSetAttribute(k_ens_phase<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256));
 }
 
 template <typename T>

@@ -82,6 +82,8 @@ SIGNATURES = [
     ("dgswem_kernel_times", C.c_int, [_vp, C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int32,
                                       C.POINTER(C.c_int32)]),
     ("dgswem_graph_info", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    ("dgswem_tune_log", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_float), C.c_int32,
+                                  C.POINTER(C.c_int32)]),
     ("dgswem_ensemble_create", C.c_int, [C.c_int32, C.POINTER(C.POINTER(Mesh)), C.POINTER(_dp),
                                          C.POINTER(Params), C.POINTER(Init), C.POINTER(Tuning), C.POINTER(_vp)]),
     ("dgswem_ensemble_get_state", C.c_int, [_vp, C.c_int32, _dp, _dp, _dp]),
@@ -181,6 +183,13 @@ class _Handle:
         k, v, b = C.c_int32(), C.c_int32(), C.c_int32()
         self._check(self.lib.dgswem_graph_info(self.h, C.byref(k), C.byref(v), C.byref(b)))
         return k.value, v.value, b.value
+
+    def tune_log(self):
+        cap = 64
+        v, b, ms = (C.c_int32 * cap)(), (C.c_int32 * cap)(), (C.c_float * cap)()
+        n = C.c_int32()
+        self._check(self.lib.dgswem_tune_log(self.h, v, b, ms, cap, C.byref(n)))
+        return [(int(v[i]), int(b[i]), float(ms[i])) for i in range(min(n.value, cap))]
 
     def set_kernel_timing(self, on: bool):
         self._check(self.lib.dgswem_set_kernel_timing(self.h, 1 if on else 0))

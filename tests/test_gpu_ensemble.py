@@ -1,4 +1,4 @@
-"""Batched ensemble: every member must equal the same scenario run alone (bitwise, same kernels),
+"""Batched ensemble: every member must equal the same scenario run alone (bitwise, same tiled kernels),
 FP64 members must match the oracle, and the bounded grid barrier must turn a withheld arrival into
 DGSWEM_ETIMEOUT instead of a hang."""
 import time
@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2508_21208_gb300 import Ensemble, Model, synth
-from paper_2508_21208_gb300.dgswem import ENSEMBLE_PERSISTENT, ENSEMBLE_PHASED, VARIANT_FUSED, DgswemError
+from paper_2508_21208_gb300.dgswem import ENSEMBLE_PERSISTENT, ENSEMBLE_PHASED, VARIANT_TILED, DgswemError
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +32,8 @@ def test_members_equal_single_runs(mode):
     ens = Ensemble(meshes, bathys, members, block=64, mode=mode)
     ens.step(25)
     for i, (mi, prm, _) in enumerate(members):
-        single = Model(meshes[mi], bathys[mi], prm, variant=VARIANT_FUSED, block=128)
+        # the ensemble's element phase is the tiled update with the tile size = block
+        single = Model(meshes[mi], bathys[mi], prm, variant=VARIANT_TILED, block=64)
         assert ens.info(i)[0] == single.dt
         single.step(25)
         a, b = ens.state(i), single.state()

@@ -193,6 +193,22 @@ def test_mixed_precision_error_bound():
     assert abs(ma[1] - mb[1]) <= 1e-9 * mb[1]
 
 
+def test_mixed_precision_storm_error_bound():
+    """Mixed form with the hurricane evaluated at element vertices in float, against the FP64
+    oracle: surface elevation and discharge stay within small absolute bounds."""
+    c = synth.config3(n=40, precision=synth.FP32_MIXED)
+    g = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal)
+    prm = dict(c.params)
+    prm["precision"] = synth.FP64
+    o = oracle.Oracle(c.mesh, c.bathy, prm, init_nodal=c.init_nodal, omp=True)
+    g.step(100)
+    o.step(100)
+    a, b = g.state(), o.state()
+    assert np.abs(b[1:]).max() > 1e-4                      # the storm moved water
+    assert np.abs(a[0, 0] - b[0, 0]).max() <= 1e-4          # metres
+    assert np.abs(a[1:, 0] - b[1:, 0]).max() <= 1e-3 * np.abs(b[1:, 0]).max() + 1e-6
+
+
 @pytest.mark.parametrize("variant", [VARIANT_SPLIT, VARIANT_TILED])
 def test_bitwise_deterministic(variant):
     c = synth.config2(n=40)
