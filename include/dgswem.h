@@ -112,7 +112,25 @@ typedef struct {
   int32_t hurricane; /* 1: Holland vortex wind stress and pressure gradient */
   double pc_hpa, pn_hpa, rmax_m, holland_b, vt_ms, track_x0, track_y0, track_heading;
   double rho_air, rho_water;
+  int32_t rk_scheme;     /* DGSWEM_RK_* (0 = SSP(2,2)) */
+  int32_t rk_stages;     /* DGSWEM_RK_CUSTOM: number of stages s, 2 <= s <= 8 */
+  double rk_coeffs[24];  /* DGSWEM_RK_CUSTOM: (a_i, b_i, c_i) for i = 1..s, see below */
 } dgswem_params;
+
+/* SSP Runge-Kutta schemes in the two-register Shu-Osher form (Sec. 2.2: the paper uses SSPRK
+ * schemes optimised for DG, Kubatko et al. 2014): u^(0) = u^n,
+ * u^(i) = a_i u^n + b_i u^(i-1) + c_i dt L(u^(i-1)), i = 1..s, u^(n+1) = u^(s); the limiter and
+ * wet/dry run after every stage; stage i sees boundary data and forcing at t_n + tau_(i-1) dt with
+ * tau_0 = 0, tau_i = b_i tau_(i-1) + c_i.  Any scheme of this form (e.g. DG-optimised
+ * coefficients) can be given as DGSWEM_RK_CUSTOM.  The CFL number is not rescaled: choose cfl
+ * (or dt) for the scheme's stability region. */
+#define DGSWEM_RK_SSP22 0  /* Shu-Osher SSP(2,2) */
+#define DGSWEM_RK_SSP33 1  /* Shu-Osher SSP(3,3) */
+#define DGSWEM_RK_SSP32 2  /* SSP(3,2): s-1 Euler steps of dt/(s-1), then the average (Ketcheson 2008) */
+#define DGSWEM_RK_SSP42 3  /* SSP(4,2), same family */
+#define DGSWEM_RK_SSP52 4  /* SSP(5,2), same family */
+#define DGSWEM_RK_SSP43 5  /* SSP(4,3) (Spiteri & Ruuth 2002) */
+#define DGSWEM_RK_CUSTOM 6
 
 /* Tuning knobs; pass NULL to dgswem_create for the defaults (all zero = automatic). */
 typedef struct {

@@ -44,7 +44,8 @@ class Params(C.Structure):
                 ("pc_hpa", C.c_double), ("pn_hpa", C.c_double), ("rmax_m", C.c_double),
                 ("holland_b", C.c_double), ("vt_ms", C.c_double), ("track_x0", C.c_double),
                 ("track_y0", C.c_double), ("track_heading", C.c_double), ("rho_air", C.c_double),
-                ("rho_water", C.c_double)]
+                ("rho_water", C.c_double), ("rk_scheme", C.c_int32), ("rk_stages", C.c_int32),
+                ("rk_coeffs", C.c_double * 24)]
 
 
 FIELD_CB = C.CFUNCTYPE(None, C.c_double, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double))
@@ -82,6 +83,7 @@ def _lib(omp: bool = False):
     lib.orc_edge_rule.restype = C.c_int32
     lib.orc_set_mms.argtypes = [C.c_void_p, FIELD_CB, FIELD_CB]
     lib.orc_project.argtypes = [C.c_void_p, FIELD_CB, C.c_double]
+    lib.orc_set_transmissive.argtypes = [C.c_void_p, C.c_int32]
     lib.orc_l2err.argtypes = [C.c_void_p, FIELD_CB, C.c_double, _dp]
     _LIBS[key] = lib
     return lib
@@ -94,7 +96,11 @@ def _ptr(a, ct=C.c_double):
 def make_params(d: dict) -> Params:
     prm = Params()
     for name, _ in Params._fields_:
-        setattr(prm, name, d[name])
+        if name == "rk_coeffs":
+            vals = list(d.get(name) or [])
+            prm.rk_coeffs = (C.c_double * 24)(*(vals + [0.0] * (24 - len(vals))))
+        else:
+            setattr(prm, name, d[name])
     return prm
 
 
@@ -192,6 +198,9 @@ class Oracle:
         cbs = (_field_cb(src_fn), _field_cb(bnd_fn))
         self._cbs.append(cbs)
         self.lib.orc_set_mms(self.h, cbs[0], cbs[1])
+
+    def set_transmissive(self, on=True):
+        self.lib.orc_set_transmissive(self.h, 1 if on else 0)
 
     def project(self, fn, t=0.0):
         cb = _field_cb(fn)

@@ -33,8 +33,12 @@
  *   - h_b is given at nodes and linear in each element; forcing is nodal and
  *     linear in each element;
  *   - friction tau_b = g n^2 |q| / H^(7/3) (Manning) or C_f |q| / H^2 (quadratic);
- *   - SSP-RK2 in Shu-Osher form; boundary data and forcing at t_n (stage 1) and
- *     t_n + dt (stage 2);
+ *   - SSP Runge-Kutta (Sec. 2.2: Shu-Osher SSPRK; the paper's production scheme is a DG-optimised
+ *     SSPRK(s,q), Kubatko et al. 2014) in the two-register Shu-Osher form
+ *     u^(i) = a_i u^n + b_i u^(i-1) + c_i dt L(u^(i-1)): SSP(2,2) (default) and SSP(3,3)
+ *     (Shu & Osher 1988), SSP(s,2) for s = 3, 4, 5 (Ketcheson 2008), SSP(4,3) (Spiteri & Ruuth
+ *     2002), or caller coefficients; boundary data and forcing of stage i at t_n + tau_(i-1) dt with
+ *     tau_0 = 0, tau_i = b_i tau_(i-1) + c_i;
  *   - limiter: Cockburn-Shu minmod limiter for triangles (nu = 1.5) on the linear
  *     modes of each variable; wet/dry: mean-preserving vertex-depth fix (Bunya et
  *     al. 2009 style), see wetdry() below;
@@ -68,6 +72,9 @@ typedef struct {
   int32_t hurricane;
   double pc_hpa, pn_hpa, rmax_m, holland_b, vt_ms, track_x0, track_y0, track_heading;
   double rho_air, rho_water;
+  int32_t rk_scheme; /* 0 SSP(2,2), 1 SSP(3,3), 2 SSP(3,2), 3 SSP(4,2), 4 SSP(5,2), 5 SSP(4,3), 6 custom */
+  int32_t rk_stages; /* custom: number of stages */
+  double rk_coeffs[24]; /* custom: (a_i, b_i, c_i) per stage */
 } orc_params;
 
 typedef void (*orc_field_cb)(double t, int32_t n, const double *xy, double *out);
@@ -103,6 +110,7 @@ typedef struct {
   int64_t nstep;
   /* test-only manufactured-solution hooks */
   orc_field_cb mms_src, mms_bnd;
+  int transmissive; /* test-only: every boundary ghost equals the interior trace */
   double *QXY;  /* physical coordinates of all area quadrature points [e][i][2] */
   double *QSRC; /* source values there [e][i][3] */
   double *BXY, *BVAL;
@@ -660,7 +668,9 @@ static void edge_integrals(orc *o, int irk, double ts) {
     for (int i = 0; i < nq; ++i) {
       double wp[3], F[3], hb = edge_hb(o, L, i);
       trace(o, irk, ep, lp, i, wp);
-      if (o->mms_bnd) {
+      if (o->transmissive) {
+        llf(P->g, wp, wp, hb, nx, ny, F);
+      } else if (o->mms_bnd) {
         int bi = -1;
         for (int b = 0; b < o->nbnd; ++b)
           if (o->BLIST[b] == L) { bi = b; break; }
@@ -843,18 +853,56 @@ static void postprocess(orc *o, int irk) {
   if (wetdry_on(o)) wetdry(o, irk);
 }
 
-/* one SSP-RK2 step in Shu-Osher form: u1 = u + dt L(u); u_new = u/2 + (u1 + dt L(u1))/2 */
-static void ssprk2_step(orc *o) {
+/* stage coefficients (a_i, b_i, c_i) of the two-register Shu-Osher form; returns the stage count */
+static int rk_table(const orc_params *P, double a[8], double b[8], double c[8]) {
+  int s = 0;
+#define ST(A, B, C) do { a[s] = (A); b[s] = (B); c[s] = (C); ++s; } while (0)
+  switch (P->rk_scheme) {
+    case 0: /* SSP(2,2) */
+      ST(0.0, 1.0, 1.0); ST(0.5, 0.5, 0.5);
+      break;
+    case 1: /* SSP(3,3) */
+      ST(0.0, 1.0, 1.0); ST(0.75, 0.25, 0.25); ST(1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0);
+      break;
+    case 2: case 3: case 4: { /* SSP(s,2): s-1 forward Euler steps of dt/(s-1), then the average */
+      const int n = P->rk_scheme + 1;
+      for (int i = 0; i < n - 1; ++i) ST(0.0, 1.0, 1.0 / (n - 1));
+      ST(1.0 / n, (n - 1.0) / n, 1.0 / n);
+      break;
+    }
+    case 5: /* SSP(4,3) */
+      ST(0.0, 1.0, 0.5); ST(0.0, 1.0, 0.5); ST(2.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0); ST(0.0, 1.0, 0.5);
+      break;
+    case 6:
+      for (int i = 0; i < P->rk_stages && i < 8; ++i)
+        ST(P->rk_coeffs[3 * i], P->rk_coeffs[3 * i + 1], P->rk_coeffs[3 * i + 2]);
+      break;
+    default:
+      return 0;
+  }
+#undef ST
+  return s;
+}
+
+/* one SSP-RK step: u^(0) = u^n, u^(i) = a_i u^n + b_i u^(i-1) + c_i dt L(u^(i-1)), limiter and
+ * wet/dry after every stage, u^(n+1) = u^(s); buffers: 0 = u^n, 1 and 2 alternate */
+static void ssprk_step(orc *o) {
   const double dt = o->dt;
-  double tn = o->t0 + (double)o->nstep * dt, tn1 = o->t0 + (double)(o->nstep + 1) * dt;
+  double a[8], b[8], c[8];
+  const int s = rk_table(&o->prm, a, b, c);
   size_t n = (size_t)3 * o->nd * o->ne;
-  double *U0 = o->U, *U1 = o->U + n;
-  eval_L(o, 0, tn);
-  for (size_t i = 0; i < n; ++i) U1[i] = U0[i] + dt * o->RHS[i];
-  postprocess(o, 1);
-  eval_L(o, 1, tn1);
-  for (size_t i = 0; i < n; ++i) U0[i] = 0.5 * U0[i] + 0.5 * (U1[i] + dt * o->RHS[i]);
-  postprocess(o, 0);
+  double tau = 0.0;
+  int prev = 0;
+  for (int i = 0; i < s; ++i) {
+    double ts = o->t0 + ((double)o->nstep + tau) * dt;
+    eval_L(o, prev, ts);
+    int out = (i == s - 1) ? 0 : (i % 2 == 0 ? 1 : 2);
+    double *U0 = o->U, *Up = o->U + (size_t)prev * n, *Uo = o->U + (size_t)out * n;
+    for (size_t k = 0; k < n; ++k) Uo[k] = a[i] * U0[k] + b[i] * Up[k] + c[i] * dt * o->RHS[k];
+    postprocess(o, out);
+    prev = out;
+    tau = b[i] * tau + c[i];
+  }
   o->nstep++;
 }
 
@@ -905,6 +953,11 @@ orc *orc_create(int32_t nn, int32_t ne, const double *xy, const int32_t *tri, in
                 const double *init_nodal, const double *init_modal, double t0) {
   if (nn <= 0 || ne <= 0 || !xy || !tri || !hb || !prm) return NULL;
   if (prm->p < 1 || prm->p > 2) return NULL;
+  {
+    double a[8], b[8], c[8];
+    int st = rk_table(prm, a, b, c);
+    if (st < 2) return NULL;
+  }
   orc *o = calloc(1, sizeof(orc));
   o->prm = *prm;
   o->p = prm->p;
@@ -920,7 +973,7 @@ orc *orc_create(int32_t nn, int32_t ne, const double *xy, const int32_t *tri, in
   if (build_geometry(o) || build_edges(o, nb, bedge, btype)) { orc_destroy(o); return NULL; }
   build_limiter_geometry(o);
   size_t n = (size_t)3 * o->nd * ne;
-  o->U = calloc(2 * n, sizeof(double));
+  o->U = calloc(3 * n, sizeof(double));
   o->RHS = calloc(n, sizeof(double));
   o->EDGE = calloc(3 * n, sizeof(double));
   o->WD = calloc(ne, 1);
@@ -976,7 +1029,7 @@ int32_t orc_sizes(const orc *o, int32_t *out) {
 }
 
 void orc_step(orc *o, int32_t n) {
-  for (int i = 0; i < n; ++i) ssprk2_step(o);
+  for (int i = 0; i < n; ++i) ssprk_step(o);
 }
 
 /* state as [3][nd][ne] arrays (zeta, qx, qy) in the caller's element order */
@@ -1092,6 +1145,10 @@ void orc_set_mms(orc *o, orc_field_cb src, orc_field_cb bnd) {
     b++;
   }
 }
+
+/* test-only: boundary ghosts equal the interior trace (zero-gradient), so a uniform state has a
+ * vanishing spatial operator and evolves by the time integrator alone */
+void orc_set_transmissive(orc *o, int32_t on) { o->transmissive = on; }
 
 /* L2 projection of a callback field onto the modes (high-order rule) */
 void orc_project(orc *o, orc_field_cb f, double t) {

@@ -49,6 +49,8 @@ int check_params(const dgswem_params *p, std::string &msg) {
       msg = "params: hurricane needs rho_air, rho_water, rmax_m, holland_b > 0"; return DGSWEM_EINVAL;
     }
   }
+  double a[MAX_STAGES], b[MAX_STAGES], c[MAX_STAGES], tau[MAX_STAGES];
+  if (rk_stage_table(*p, a, b, c, tau) < 2) { msg = "params: unknown Runge-Kutta scheme or bad table"; return DGSWEM_EINVAL; }
   return 0;
 }
 
@@ -146,6 +148,7 @@ static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
   const size_t nu = 3 * (size_t)ND * ne;
   c->U0 = k.take<double>(nu);
   c->U1 = k.take<double>(nu);
+  c->U2 = c->nst >= 3 ? k.take<double>(nu) : nullptr;
   c->mean = k.take<double>(3 * (size_t)ne);
   c->wd = k.take<uint8_t>(ne);
   c->wd_stage = k.take<uint8_t>(ne);
@@ -221,14 +224,15 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
   const LaunchCfg cfg{block, c->st};
   const Phys &ph = c->ph;
   int ev_i = 0;
-  for (int stage = 0; stage < 2; ++stage) {
-    double *uin = stage ? c->U1 : c->U0;
-    double *out = stage ? c->U0 : c->U1;
+  for (int stage = 0; stage < c->nst; ++stage) {
+    // stage 0 reads u^n (U0); intermediate stages alternate U1 / U2; the last writes over U0
+    double *uin = stage == 0 ? c->U0 : ((stage - 1) % 2 == 0 ? c->U1 : c->U2);
+    double *out = stage == c->nst - 1 ? c->U0 : (stage % 2 == 0 ? c->U1 : c->U2);
     const Clock clk{c->step, c->t0, c->dt};
     const bool inline_frc = ph.hurricane && c->mixed;  // mixed form: vortex evaluated per element vertex
     if (ph.hurricane && !inline_frc) {
       mark(c, kname_forcing, names, &ev_i);
-      launch_forcing(c->mixed, c->dm, ph, clk, stage, 0.0, c->frc, cfg);
+      launch_forcing(c->mixed, c->dm, ph, clk, c->rtau[stage], 0.0, c->frc, cfg);
     }
     StageArgs sa{};
     sa.uin = uin;
@@ -241,7 +245,10 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
     sa.frc = (ph.hurricane && !inline_frc) ? c->frc : nullptr;
     sa.frc_inline = inline_frc ? 1 : 0;
     sa.clk = clk;
-    sa.stage = stage;
+    sa.tau = c->rtau[stage];
+    sa.ra = c->ra[stage];
+    sa.rb = c->rb[stage];
+    sa.rc = c->rc[stage];
     sa.err = c->err;
     if (variant == DGSWEM_VARIANT_TILED) {
       mark(c, kname_element, names, &ev_i);
@@ -268,9 +275,9 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
 }
 
 static int kernels_in_step(const dgswem_ctx *c, int variant) {
-  int per_stage = 1 + ((c->ph.hurricane && !c->mixed) ? 1 : 0) + ((variant == DGSWEM_VARIANT_SPLIT && c->dm.nint > 0) ? 1 : 0) +
+  const int per_stage = 1 + ((c->ph.hurricane && !c->mixed) ? 1 : 0) + ((variant == DGSWEM_VARIANT_SPLIT && c->dm.nint > 0) ? 1 : 0) +
                   ((c->ph.limiter || c->ph.wetdry) ? 1 : 0);
-  return 2 * per_stage + 1;
+  return c->nst * per_stage + 1;
 }
 
 static void destroy_graph(dgswem_ctx *c) {
@@ -395,6 +402,7 @@ int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_par
   c->P = params->p;
   c->ND = nd_of(c->P);
   c->mixed = params->precision == DGSWEM_FP32_MIXED;
+  c->nst = rk_stage_table(*params, c->ra, c->rb, c->rc, c->rtau);
   int r = preprocess_mesh(*mesh, bathy, c->tun.reorder != 2, c->hm, msg);
   if (r) {
     delete c;
@@ -650,7 +658,7 @@ int dgswem_eval_rhs(dgswem_ctx *c, double t, double *h_out) {
   if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
   const LaunchCfg cfg{c->block, c->st};
   const bool inline_frc = c->ph.hurricane && c->mixed;
-  if (c->ph.hurricane && !inline_frc) launch_forcing(c->mixed, c->dm, c->ph, Clock{nullptr, 0, 0}, 0, t, c->frc, cfg);
+  if (c->ph.hurricane && !inline_frc) launch_forcing(c->mixed, c->dm, c->ph, Clock{nullptr, 0, 0}, 0.0, t, c->frc, cfg);
   StageArgs sa{};
   sa.uin = c->U0;
   sa.un = c->U0;
@@ -662,7 +670,10 @@ int dgswem_eval_rhs(dgswem_ctx *c, double t, double *h_out) {
   sa.frc = (c->ph.hurricane && !inline_frc) ? c->frc : nullptr;
   sa.frc_inline = inline_frc ? 1 : 0;
   sa.clk = Clock{nullptr, 0.0, c->dt};
-  sa.stage = 0;
+  sa.tau = 0.0;
+  sa.ra = 0.0;
+  sa.rb = 1.0;
+  sa.rc = 1.0;
   sa.err = c->err;
   sa.tide_t = t;
   const bool split = c->variant == DGSWEM_VARIANT_SPLIT;
@@ -709,7 +720,7 @@ int dgswem_eval_forcing(dgswem_ctx *c, double t, double *h_out) {
   if (c->sticky) return c->sticky;
   if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
   if (!c->ph.hurricane) return ctx_fail(c, DGSWEM_EINVAL, "no hurricane forcing configured");
-  launch_forcing(c->mixed, c->dm, c->ph, Clock{nullptr, 0, 0}, 0, t, c->frc, LaunchCfg{256, c->st});
+  launch_forcing(c->mixed, c->dm, c->ph, Clock{nullptr, 0, 0}, 0.0, t, c->frc, LaunchCfg{256, c->st});
   const size_t n = 3 * (size_t)c->hm.nn;
   std::vector<char> buf(n * (c->mixed ? 4 : 8));
   if (int r = ctx_cuda(c, cudaMemcpyAsync(buf.data(), c->frc, buf.size(), cudaMemcpyDeviceToHost, c->st), "forcing readback"))

@@ -38,6 +38,8 @@ struct dgswem_ctx {
   std::vector<double> init_modal, init_nodal;
   double t0 = 0.0, dt = 0.0;
   int64_t steps_done = 0;
+  int nst = 2;  // Runge-Kutta stages
+  double ra[dg::MAX_STAGES] = {}, rb[dg::MAX_STAGES] = {}, rc[dg::MAX_STAGES] = {}, rtau[dg::MAX_STAGES] = {};
   // device side
   size_t need = 0, ws_bytes = 0;
   char *ws = nullptr;
@@ -48,7 +50,7 @@ struct dgswem_ctx {
   dg::TileEdges htiles;
   dg::Phys ph{};
   int *d_perm = nullptr, *d_iperm = nullptr;
-  double *U0 = nullptr, *U1 = nullptr, *mean = nullptr, *partial = nullptr, *result = nullptr,
+  double *U0 = nullptr, *U1 = nullptr, *U2 = nullptr, *mean = nullptr, *partial = nullptr, *result = nullptr,
          *staging = nullptr;
   uint8_t *wd = nullptr, *wd_stage = nullptr, *emode = nullptr;
   void *eflux = nullptr, *frc = nullptr;

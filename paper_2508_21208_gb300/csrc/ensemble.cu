@@ -22,7 +22,7 @@ struct EnsMember {
   int init_kind = 0;
   std::vector<double> init_modal, init_nodal;
   double t0 = 0.0, dt = 0.0;
-  double *U0 = nullptr, *U1 = nullptr, *mean = nullptr;
+  double *U0 = nullptr, *U1 = nullptr, *U2 = nullptr, *mean = nullptr;
   uint8_t *wd = nullptr;
   void *frc = nullptr;
 };
@@ -74,6 +74,7 @@ static void ens_layout(dgswem_ctx *c, char *base, size_t *bytes) {
     const size_t nu = 3 * (size_t)ND * H.ne;
     mb.U0 = k.take<double>(nu);
     mb.U1 = k.take<double>(nu);
+    mb.U2 = c->nst >= 3 ? k.take<double>(nu) : nullptr;
     mb.mean = k.take<double>(3 * (size_t)H.ne);
     mb.wd = k.take<uint8_t>(H.ne);
     mb.frc = k.take<char>(tsz * 3 * H.nn);
@@ -107,6 +108,7 @@ static void build_tiles(dgswem_ctx *c, int block) {
     d.ph = mb.ph;
     d.U0 = mb.U0;
     d.U1 = mb.U1;
+    d.U2 = mb.U2;
     d.mean = mb.mean;
     d.wd = mb.wd;
     d.frc = mb.frc;
@@ -183,6 +185,13 @@ static int grid_for(dgswem_ctx *c, int block) {
 void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names) {
   EnsembleState &E = *c->ens;
   EnsArgs a{};
+  a.nstages = c->nst;
+  for (int i = 0; i < c->nst; ++i) {
+    a.ra[i] = c->ra[i];
+    a.rb[i] = c->rb[i];
+    a.rc[i] = c->rc[i];
+    a.tau[i] = c->rtau[i];
+  }
   a.mem = E.d_mem;
   a.etile = E.d_etile;
   a.ntile = E.d_ntile;
@@ -202,7 +211,7 @@ void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names) {
   if (e != cudaSuccess) ctx_cuda(c, e, "ensemble launch");
   if (!E.persistent) launch_advance(c->step, c->st);
   if (names) cudaEventRecordWithFlags(c->ev[1], c->st, cudaEventRecordExternal);
-  c->kernels_per_step = E.persistent ? 1 : 2 * ((E.n_ntile > 0) + 1 + E.any_limwd) + 1;
+  c->kernels_per_step = E.persistent ? 1 : c->nst * ((E.n_ntile > 0) + 1 + E.any_limwd) + 1;
 }
 
 static int upload_mesh_tiles(dgswem_ctx *c, EnsMesh &M, int tile) {
@@ -341,6 +350,11 @@ int dgswem_ensemble_create(int32_t n, const dgswem_mesh *const *meshes, const do
     if (!meshes[i] || !bathy[i]) return DGSWEM_EINVAL;
     if (check_params(&params[i], msg)) return DGSWEM_EINVAL;
     if (params[i].p != params[0].p || params[i].precision != params[0].precision) return DGSWEM_EINVAL;
+    if (params[i].rk_scheme != params[0].rk_scheme) return DGSWEM_EINVAL;
+    if (params[i].rk_scheme == DGSWEM_RK_CUSTOM &&
+        (params[i].rk_stages != params[0].rk_stages ||
+         std::memcmp(params[i].rk_coeffs, params[0].rk_coeffs, sizeof(params[0].rk_coeffs)) != 0))
+      return DGSWEM_EINVAL;
   }
   dgswem_ctx *c = new dgswem_ctx();
   c->ensemble = true;
@@ -354,6 +368,7 @@ int dgswem_ensemble_create(int32_t n, const dgswem_mesh *const *meshes, const do
   c->P = params[0].p;
   c->ND = nd_of(c->P);
   c->mixed = params[0].precision == DGSWEM_FP32_MIXED;
+  c->nst = rk_stage_table(params[0], c->ra, c->rb, c->rc, c->rtau);
   c->ens = new EnsembleState();
   EnsembleState &E = *c->ens;
   for (int i = 0; i < n; ++i) {

@@ -104,8 +104,14 @@ struct DevMesh {
 
 struct Clock {
   const long long *step;   // device counter of completed steps
-  double t0, dt;           // stage time = t0 + (step + stage) * dt
+  double t0, dt;           // stage time = t0 + (step + tau) * dt
 };
+
+constexpr int MAX_STAGES = 8;
+// Two-register Shu-Osher stage table: u_i = a_i u^n + b_i u_(i-1) + c_i dt L(u_(i-1)); stage i
+// evaluates L at tau_(i-1).  Returns the stage count (0 if the parameters name no valid scheme).
+int rk_stage_table(const dgswem_params &p, double a[MAX_STAGES], double b[MAX_STAGES], double c[MAX_STAGES],
+                   double tau[MAX_STAGES]);
 
 struct StageArgs {
   const double *uin;       // u^(s): [3][ND][ne]
@@ -118,7 +124,8 @@ struct StageArgs {
   const void *frc;         // T [3][nn] nodal forcing at the stage time, or nullptr
   int frc_inline;          // 1: evaluate the forcing at the element's vertices (mixed form)
   Clock clk;
-  int stage;
+  double tau;              // stage time = clk.t0 + (step + tau) * clk.dt
+  double ra, rb, rc;       // u_out = ra u^n + rb u_in + rc dt L(u_in)
   int *err;
   double tide_t;           // stage time when clk.step is null (single operator calls)
 };
@@ -138,7 +145,7 @@ struct MemberDev {
   DevMesh m;               // the member's mesh statics (shared with members on the same mesh)
   DevTiles tl;             // the mesh's tile edge lists for the ensemble's tile size
   Phys ph;
-  double *U0, *U1, *mean;  // its own state
+  double *U0, *U1, *U2, *mean;  // its own state (U2 only for three or more stages)
   uint8_t *wd;
   void *frc;               // T [3][nn]
   double t0, dt;           // stage time = t0 + (step + stage) * dt (its own dt)
@@ -146,6 +153,8 @@ struct MemberDev {
 };
 
 struct EnsArgs {
+  int nstages;
+  double ra[MAX_STAGES], rb[MAX_STAGES], rc[MAX_STAGES], tau[MAX_STAGES];
   const MemberDev *mem;
   const int *etile;        // element tile -> member
   const int *ntile;        // node tile -> member (members with a hurricane)
@@ -189,7 +198,7 @@ struct LaunchCfg {
 };
 #define DG_DECLARE_LAUNCHERS(SUF)                                                                 \
   void upload_tables_##SUF(const Tab<double> td[2]);                                             \
-  void launch_forcing_##SUF(const DevMesh &m, const Phys &ph, const Clock &clk, int stage,       \
+  void launch_forcing_##SUF(const DevMesh &m, const Phys &ph, const Clock &clk, double tau,      \
                             double t_fixed, void *frc, const LaunchCfg &c);                      \
   void launch_edge_##SUF(int p, const DevMesh &m, const StageArgs &s, const Phys &ph,            \
                          const LaunchCfg &c);                                                    \
@@ -208,10 +217,10 @@ DG_DECLARE_LAUNCHERS(f64)
 DG_DECLARE_LAUNCHERS(f32)
 #undef DG_DECLARE_LAUNCHERS
 
-inline void launch_forcing(bool mixed, const DevMesh &m, const Phys &ph, const Clock &clk, int stage,
+inline void launch_forcing(bool mixed, const DevMesh &m, const Phys &ph, const Clock &clk, double tau,
                            double t_fixed, void *frc, const LaunchCfg &c) {
-  mixed ? launch_forcing_f32(m, ph, clk, stage, t_fixed, frc, c)
-        : launch_forcing_f64(m, ph, clk, stage, t_fixed, frc, c);
+  mixed ? launch_forcing_f32(m, ph, clk, tau, t_fixed, frc, c)
+        : launch_forcing_f64(m, ph, clk, tau, t_fixed, frc, c);
 }
 inline void launch_edge(bool mixed, int p, const DevMesh &m, const StageArgs &s, const Phys &ph,
                         const LaunchCfg &c) {

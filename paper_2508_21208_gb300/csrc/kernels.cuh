@@ -20,8 +20,8 @@ __device__ __forceinline__ const Tab<double> &ctab<double>(int p) { return c_td[
 template <>
 __device__ __forceinline__ const Tab<float> &ctab<float>(int p) { return c_tf[p - 1]; }
 
-__device__ __forceinline__ double stage_time(const Clock &c, int stage, double fixed) {
-  return c.step ? c.t0 + (double)(*c.step + stage) * c.dt : fixed;
+__device__ __forceinline__ double stage_time(const Clock &c, double tau, double fixed) {
+  return c.step ? c.t0 + ((double)*c.step + tau) * c.dt : fixed;
 }
 
 // ------------------------------------------------------------------------ conversions
@@ -255,11 +255,11 @@ __device__ __forceinline__ void forcing_body(const double *nodexy, int nn, const
 }
 
 template <typename T>
-__global__ void k_forcing(const double *nodexy, int nn, Phys ph, Clock clk, int stage, double t_fixed,
+__global__ void k_forcing(const double *nodexy, int nn, Phys ph, Clock clk, double tau, double t_fixed,
                           T *frc) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
-  forcing_body<T>(nodexy, nn, ph, stage_time(clk, stage, t_fixed), frc, n);
+  forcing_body<T>(nodexy, nn, ph, stage_time(clk, tau, t_fixed), frc, n);
 }
 
 // Copy the edge basis table of degree P into shared memory (indexed by thread-varying local edges).
@@ -470,7 +470,7 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
       if (s.frc_inline) {
         // the centre once per element; vertex offsets in T (O(1e5) m coordinates, float ulp ~1 cm)
         double cxd, cyd;
-        storm_center(ph, stage_time(s.clk, s.stage, s.tide_t), cxd, cyd);
+        storm_center(ph, stage_time(s.clk, s.tau, s.tide_t), cxd, cyd);
         const T cx = from_d<T>(cxd), cy = from_d<T>(cyd);
         vortex_at<T>(ph, from_d<T>(m.nodexy[n0]) - cx, from_d<T>(m.nodexy[nn + n0]) - cy, t0, u0, p0);
         vortex_at<T>(ph, from_d<T>(m.nodexy[n1]) - cx, from_d<T>(m.nodexy[nn + n1]) - cy, t1, u1, p1);
@@ -522,11 +522,13 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
       double out;
       if (write_rhs) {
         out = Ld;
-      } else if (s.stage == 0) {
-        out = s.uin[ix] + dt * Ld;
-      } else {
+      } else if (s.ra == 0.0 && s.rb == 1.0) {  // forward-Euler stage
+        out = s.uin[ix] + (s.rc * dt) * Ld;
+      } else if (s.ra == 0.5 && s.rb == 0.5 && s.rc == 0.5) {
         // u/2 + (u1 + dt L)/2 == (u + (u1 + dt L)) / 2 exactly (halving commutes with rounding)
         out = half_exact(s.un[ix] + (s.uin[ix] + dt * Ld));
+      } else {
+        out = fma(s.rc * dt, Ld, s.ra * s.un[ix] + s.rb * s.uin[ix]);
       }
       bad |= !finite_bits(out);
       s.uout[ix] = out;
@@ -624,7 +626,7 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
         }
       }
       if (j == NBR_OPEN) {
-        const double ts = stage_time(s.clk, s.stage, s.tide_t);
+        const double ts = stage_time(s.clk, s.tau, s.tide_t);
         const T zt = from_d<T>(ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase));
 #pragma unroll
         for (int q = 0; q < NQE; ++q) {
@@ -769,7 +771,7 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
       for (int v = 0; v < 3; ++v) slot(a - e0, la, q, v) = hl * tb.we[q] * f[v];
     }
   } else {
-    const double ts = stage_time(s.clk, s.stage, s.tide_t);
+    const double ts = stage_time(s.clk, s.tau, s.tide_t);
     const T zt = from_d<T>(ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase));
 #pragma unroll
     for (int q = 0; q < NQE; ++q) {
@@ -1090,13 +1092,23 @@ __device__ __forceinline__ bool grid_barrier(const EnsArgs &a, bool skip) {
   return (*(volatile int *)a.err & ERR_TIMEOUT) == 0;
 }
 
+// Buffers of stage i of s: stage 0 reads u^n (U0); intermediate stages alternate U1 / U2; the last
+// stage writes u^(n+1) over U0 (each element reads only its own u^n there).
+__device__ __forceinline__ void stage_buffers(int i, int s, double *U0, double *U1, double *U2, double *&in,
+                                              double *&out) {
+  in = i == 0 ? U0 : ((i - 1) % 2 == 0 ? U1 : U2);
+  out = i == s - 1 ? U0 : (i % 2 == 0 ? U1 : U2);
+}
+
 // Stage arguments of member md (no edge scratch; the mixed form evaluates forcing inline).
 template <typename T>
 __device__ __forceinline__ StageArgs member_stage(const MemberDev &md, const EnsArgs &a, int stage) {
   StageArgs sa;
-  sa.uin = stage ? md.U1 : md.U0;
+  double *in, *out;
+  stage_buffers(stage, a.nstages, md.U0, md.U1, md.U2, in, out);
+  sa.uin = in;
   sa.un = md.U0;
-  sa.uout = stage ? md.U0 : md.U1;
+  sa.uout = out;
   sa.mean = md.ph.limiter ? md.mean : nullptr;
   sa.wd = md.ph.wetdry ? md.wd : nullptr;
   sa.eflux = nullptr;
@@ -1105,7 +1117,10 @@ __device__ __forceinline__ StageArgs member_stage(const MemberDev &md, const Ens
   sa.frc = (md.ph.hurricane && !inl) ? md.frc : nullptr;
   sa.frc_inline = inl ? 1 : 0;
   sa.clk = Clock{a.step, md.t0, md.dt};
-  sa.stage = stage;
+  sa.tau = a.tau[stage];
+  sa.ra = a.ra[stage];
+  sa.rb = a.rb[stage];
+  sa.rc = a.rc[stage];
   sa.err = a.err;
   sa.tide_t = 0.0;
   return sa;
@@ -1137,7 +1152,7 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
       load_member(sd, &a.mem[a.ntile[t]]);
       const int n = (t - sd->ntile0) * blockDim.x + threadIdx.x;
       if (n < sd->m.nn)
-        forcing_body<T>(sd->m.nodexy, sd->m.nn, sd->ph, stage_time(Clock{a.step, sd->t0, sd->dt}, stage, 0.0),
+        forcing_body<T>(sd->m.nodexy, sd->m.nn, sd->ph, stage_time(Clock{a.step, sd->t0, sd->dt}, a.tau[stage], 0.0),
                         (T *)sd->frc, n);
     }
   } else {
@@ -1148,8 +1163,9 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
       if (phase == 1) {
         continue;  // handled by the tiled loop below
       } else if (sd->ph.limiter || sd->ph.wetdry) {
-        limwd_body<P, T>(sd->m, stage ? sd->U0 : sd->U1, sd->mean, sd->wd, sd->ph, a.err, sd->ph.limiter,
-                         sd->ph.wetdry, e);
+        double *in, *out;
+        stage_buffers(stage, a.nstages, sd->U0, sd->U1, sd->U2, in, out);
+        limwd_body<P, T>(sd->m, out, sd->mean, sd->wd, sd->ph, a.err, sd->ph.limiter, sd->ph.wetdry, e);
       }
     }
   }
@@ -1166,7 +1182,7 @@ __global__ void __launch_bounds__(256) k_ens_persistent(const EnsArgs a) {
   __syncthreads();
   if (*(volatile int *)a.err & ERR_TIMEOUT) return;  // an earlier step already failed
   const bool skip = a.fault && blockIdx.x == gridDim.x - 1;
-  for (int stage = 0; stage < 2; ++stage) {
+  for (int stage = 0; stage < a.nstages; ++stage) {
     if (a.n_ntile > 0) {
       ens_phase<P, T>(a, 0, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
       if (!grid_barrier(a, skip)) return;
@@ -1175,7 +1191,7 @@ __global__ void __launch_bounds__(256) k_ens_persistent(const EnsArgs a) {
     if (!grid_barrier(a, skip)) return;
     if (a.any_limwd) {
       ens_phase<P, T>(a, 2, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
-      if (stage == 0 && !grid_barrier(a, skip)) return;
+      if (stage < a.nstages - 1 && !grid_barrier(a, skip)) return;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.step += 1;
@@ -1209,7 +1225,7 @@ cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int bloc
                   : cudaLaunchKernelEx(&cfg, k_ens_persistent<2, T>, a);
   }
   const size_t sm = p == 1 ? tile_smem_bytes<1, T>(block) : tile_smem_bytes<2, T>(block);
-  for (int stage = 0; stage < 2; ++stage) {
+  for (int stage = 0; stage < a.nstages; ++stage) {
     if (a.n_ntile > 0) {
       if (p == 1) k_ens_phase<1, T><<<a.n_ntile, block, sm, s>>>(a, 0, stage);
       else k_ens_phase<2, T><<<a.n_ntile, block, sm, s>>>(a, 0, stage);
@@ -1250,9 +1266,9 @@ static inline void upload_tables_tu(const Tab<double> td[2]) {
 inline int nblocks(long n, int b) { return (int)((n + b - 1) / b); }
 
 template <typename T>
-void launch_forcing_t(const DevMesh &m, const Phys &ph, const Clock &clk, int stage, double tf, void *frc,
+void launch_forcing_t(const DevMesh &m, const Phys &ph, const Clock &clk, double tau, double tf, void *frc,
                       const LaunchCfg &c) {
-  k_forcing<T><<<nblocks(m.nn, 256), 256, 0, c.stream>>>(m.nodexy, m.nn, ph, clk, stage, tf, (T *)frc);
+  k_forcing<T><<<nblocks(m.nn, 256), 256, 0, c.stream>>>(m.nodexy, m.nn, ph, clk, tau, tf, (T *)frc);
 }
 
 template <typename T>

@@ -5,9 +5,9 @@ namespace dg {
 
 void upload_tables_f64(const Tab<double> td[2]) { upload_tables_tu(td); }
 
-void launch_forcing_f64(const DevMesh &m, const Phys &ph, const Clock &clk, int stage, double t_fixed,
+void launch_forcing_f64(const DevMesh &m, const Phys &ph, const Clock &clk, double tau, double t_fixed,
                         void *frc, const LaunchCfg &c) {
-  launch_forcing_t<double>(m, ph, clk, stage, t_fixed, frc, c);
+  launch_forcing_t<double>(m, ph, clk, tau, t_fixed, frc, c);
 }
 void launch_edge_f64(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, const LaunchCfg &c) {
   launch_edge_t<double>(p, m, s, ph, c);

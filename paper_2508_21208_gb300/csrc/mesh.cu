@@ -351,6 +351,59 @@ void build_tile_edges(const HostMesh &H, int tile, TileEdges &T) {
     }
 }
 
+// ------------------------------------------------------------------ SSP Runge-Kutta tables
+int rk_stage_table(const dgswem_params &p, double a[MAX_STAGES], double b[MAX_STAGES], double c[MAX_STAGES],
+                   double tau[MAX_STAGES]) {
+  int s = 0;
+  auto st = [&](double x, double y, double z) {
+    a[s] = x;
+    b[s] = y;
+    c[s] = z;
+    ++s;
+  };
+  switch (p.rk_scheme) {
+    case DGSWEM_RK_SSP22:  // Shu-Osher
+      st(0.0, 1.0, 1.0);
+      st(0.5, 0.5, 0.5);
+      break;
+    case DGSWEM_RK_SSP33:  // Shu-Osher
+      st(0.0, 1.0, 1.0);
+      st(0.75, 0.25, 0.25);
+      st(1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0);
+      break;
+    case DGSWEM_RK_SSP32:
+    case DGSWEM_RK_SSP42:
+    case DGSWEM_RK_SSP52: {  // Ketcheson: s-1 Euler steps of dt/(s-1), then the average with u^n
+      const int n = p.rk_scheme + 1;
+      for (int i = 0; i < n - 1; ++i) st(0.0, 1.0, 1.0 / (n - 1));
+      st(1.0 / n, (n - 1.0) / n, 1.0 / n);
+      break;
+    }
+    case DGSWEM_RK_SSP43:  // Spiteri-Ruuth
+      st(0.0, 1.0, 0.5);
+      st(0.0, 1.0, 0.5);
+      st(2.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0);
+      st(0.0, 1.0, 0.5);
+      break;
+    case DGSWEM_RK_CUSTOM:
+      if (p.rk_stages < 2 || p.rk_stages > MAX_STAGES) return 0;
+      for (int i = 0; i < p.rk_stages; ++i) {
+        const double *q = p.rk_coeffs + 3 * i;
+        if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2])) return 0;
+        st(q[0], q[1], q[2]);
+      }
+      break;
+    default:
+      return 0;
+  }
+  double t = 0.0;  // stage i evaluates L at the time of its input u_(i-1)
+  for (int i = 0; i < s; ++i) {
+    tau[i] = t;
+    t = b[i] * t + c[i];
+  }
+  return s;
+}
+
 // ------------------------------------------------------------------ reference tables
 // Dubiner basis (Sec. 2.2, Eq. dubiner) psi_ij = P_i(a) ((1-b)/2)^i P_j^(2i+1,0)(b), written out
 // for i + j <= 2, with its reference gradient.

@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("pc_hpa", C.c_double), ("pn_hpa", C.c_double), ("rmax_m", C.c_double),
                 ("holland_b", C.c_double), ("vt_ms", C.c_double), ("track_x0", C.c_double),
                 ("track_y0", C.c_double), ("track_heading", C.c_double), ("rho_air", C.c_double),
-                ("rho_water", C.c_double)]
+                ("rho_water", C.c_double), ("rk_scheme", C.c_int32), ("rk_stages", C.c_int32),
+                ("rk_coeffs", C.c_double * 24)]
 
 
 class Tuning(C.Structure):
@@ -123,7 +124,11 @@ def _torch_cuda():
 def make_params(d: dict) -> Params:
     p = Params()
     for name, _ in Params._fields_:
-        setattr(p, name, d[name])
+        if name == "rk_coeffs":
+            vals = list(d.get(name) or [])
+            p.rk_coeffs = (C.c_double * 24)(*(vals + [0.0] * (24 - len(vals))))
+        else:
+            setattr(p, name, d[name])
     return p
 
 

@@ -38,6 +38,9 @@ FRICTION_QUADRATIC = 2
 FP64 = 0
 FP32_MIXED = 1
 
+# SSP Runge-Kutta schemes (interface codes shared by both sides)
+RK_SSP22, RK_SSP33, RK_SSP32, RK_SSP42, RK_SSP52, RK_SSP43, RK_CUSTOM = range(7)
+
 
 def splitmix64(counter: np.ndarray) -> np.ndarray:
     """SplitMix64 output for each 64-bit counter value (vectorised)."""
@@ -165,7 +168,7 @@ def default_params(**kw) -> dict:
              tide_amp=0.0, tide_period=44714.0, tide_phase=0.0,
              hurricane=0, pc_hpa=950.0, pn_hpa=1013.0, rmax_m=40000.0, holland_b=1.5,
              vt_ms=5.0, track_x0=0.0, track_y0=0.0, track_heading=0.0,
-             rho_air=1.15, rho_water=1000.0)
+             rho_air=1.15, rho_water=1000.0, rk_scheme=0, rk_stages=0, rk_coeffs=None)
     for k, v in kw.items():
         if k not in p:
             raise KeyError(k)
