@@ -102,7 +102,7 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, form: str, elements: int):
+def recorded_traffic(kernel: str, form: str, elements: int, variant: int):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels."""
     p = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if not os.path.exists(p):
@@ -110,7 +110,8 @@ def recorded_traffic(kernel: str, form: str, elements: int):
     sha = kernel_source_sha()
     for line in open(p):
         kv = dict(re.findall(r"(\w+)=(\S+)", line))
-        if kv.get("kernel") == kernel and kv.get("form") == form and kv.get("src_sha") == sha:
+        if (kv.get("kernel") == kernel and kv.get("form") == form and kv.get("src_sha") == sha
+                and int(kv.get("variant", -1)) == variant):
             # captured on a larger mesh (DRAM-resident); traffic per launch scales with elements
             return float(kv["bytes"]) / float(kv["elements"]) * elements
     return None
@@ -130,6 +131,18 @@ ALG_BYTES = {("fp64", 1): 309, ("mixed", 1): 259, ("fp64", 2): 453, ("mixed", 2)
 # update 9 x 6 (the edge kernel's share is counted on the edge kernel: 2 points x 86 per edge).
 ALG_FLOPS_ELEMENT_P1 = 6 * 46 + 40 + 3 * (2 * 18 + 12) + 9 * 6
 ALG_FLOPS_EDGE_P1 = 2 * 86
+
+
+def aggregate(seconds, units, dist=None, device="cpu"):
+    """Replica aggregation: the job's time is the slowest rank's, its work the sum over ranks."""
+    if dist is None:
+        return seconds, units
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
 
 
 def make_model(case, stream, **kw):
@@ -301,13 +314,9 @@ def main():
     with ClockSampler(local) as clk:
         model, ms, kt, (kps, variant, block) = run_form(case, args.steps, args.warmup, stream, flush)
     torch.cuda.synchronize()
-    total_s = sum(ms) * 1e-3
+    total_s, units = aggregate(sum(ms) * 1e-3, case.mesh.n_elems * 2 * args.steps, dist, "cuda")
     if dist:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
         dist.barrier()
-    units = case.mesh.n_elems * 2 * args.steps * world
     value = units / total_s
     if rank != 0:
         if dist:
@@ -317,8 +326,11 @@ def main():
     hbm, hbm_kind = peaks()
     name, avg_s, tot = dominant(kt)
     ne = case.mesh.n_elems
-    if name == "element_update":
+    if name == "element_update" and variant == 1:
         flops = ALG_FLOPS_ELEMENT_P1 * ne
+    elif name == "element_update":
+        # fused and tiled variants evaluate the edge fluxes inside the element kernel
+        flops = (ALG_FLOPS_ELEMENT_P1 + 1.5 * ALG_FLOPS_EDGE_P1) * ne
     elif name == "edge_flux":
         flops = ALG_FLOPS_EDGE_P1 * 1.5 * ne
     else:
@@ -327,7 +339,7 @@ def main():
             "achieved": flops / avg_s / 1e9 if flops else None, "peak": FP64_PEAK_GFLOPS,
             "peak_kind": "derived from unit counts and clocks (FP64)",
             "frac": (flops / avg_s / 1e9) / FP64_PEAK_GFLOPS if flops else None,
-            "traffic": recorded_traffic(name, "fp64", ne),
+            "traffic": recorded_traffic(name, "fp64", ne, variant),
             "avg_launch_ms": avg_s * 1e3, "launches_per_step": 2,
             "share_of_step": tot[name] / sum(tot.values())}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -59,6 +59,8 @@ extern "C" {
 /* boundary edge types (Sec. 2.1: Gamma_land, Gamma_ocean) */
 #define DGSWEM_BC_LAND 0 /* no normal flow: mirror ghost state */
 #define DGSWEM_BC_OPEN 1 /* elevation-specified (tidal) boundary, momentum from the interior */
+#define DGSWEM_BC_RIVER 2 /* river inflow (Gamma_river): the land mirror ghost shifted so that the
+                             mean normal discharge of the two traces is -river_q (inflow) */
 
 /* arithmetic forms */
 #define DGSWEM_FP64 0       /* every step in IEEE double */
@@ -115,7 +117,15 @@ typedef struct {
   int32_t rk_scheme;     /* DGSWEM_RK_* (0 = SSP(2,2)) */
   int32_t rk_stages;     /* DGSWEM_RK_CUSTOM: number of stages s, 2 <= s <= 8 */
   double rk_coeffs[24];  /* DGSWEM_RK_CUSTOM: (a_i, b_i, c_i) for i = 1..s, see below */
+  int32_t flux;          /* numerical flux F^ of Eq. elem_weak_form: DGSWEM_FLUX_LLF or _ROE */
+  double rain_rate;      /* R of Eq. SWE: uniform rain rate (m/s) */
+  double river_q;        /* inflow discharge per unit width on DGSWEM_BC_RIVER edges (m^2/s) */
 } dgswem_params;
+
+/* numerical fluxes (Sec. 2.2: "e.g., Local Lax-Friedrichs or Roe flux") */
+#define DGSWEM_FLUX_LLF 0 /* local Lax-Friedrichs, lambda = max(|u.n| + sqrt(gH)) of the two traces */
+#define DGSWEM_FLUX_ROE 1 /* Roe (1981): Roe-averaged |A| in the edge frame, Harten entropy fix
+                             (delta = c~/10) on the two acoustic waves */
 
 /* SSP Runge-Kutta schemes in the two-register Shu-Osher form (Sec. 2.2: the paper uses SSPRK
  * schemes optimised for DG, Kubatko et al. 2014): u^(0) = u^n,

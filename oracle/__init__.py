@@ -45,7 +45,8 @@ class Params(C.Structure):
                 ("holland_b", C.c_double), ("vt_ms", C.c_double), ("track_x0", C.c_double),
                 ("track_y0", C.c_double), ("track_heading", C.c_double), ("rho_air", C.c_double),
                 ("rho_water", C.c_double), ("rk_scheme", C.c_int32), ("rk_stages", C.c_int32),
-                ("rk_coeffs", C.c_double * 24)]
+                ("rk_coeffs", C.c_double * 24), ("flux", C.c_int32), ("rain_rate", C.c_double),
+                ("river_q", C.c_double)]
 
 
 FIELD_CB = C.CFUNCTYPE(None, C.c_double, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double))
@@ -84,6 +85,7 @@ def _lib(omp: bool = False):
     lib.orc_set_mms.argtypes = [C.c_void_p, FIELD_CB, FIELD_CB]
     lib.orc_project.argtypes = [C.c_void_p, FIELD_CB, C.c_double]
     lib.orc_set_transmissive.argtypes = [C.c_void_p, C.c_int32]
+    lib.orc_numflux.argtypes = [C.POINTER(Params), _dp, _dp, C.c_double, C.c_double, C.c_double, _dp]
     lib.orc_l2err.argtypes = [C.c_void_p, FIELD_CB, C.c_double, _dp]
     _LIBS[key] = lib
     return lib
@@ -211,6 +213,15 @@ class Oracle:
         out = (C.c_double * 3)()
         self.lib.orc_l2err(self.h, cb, float(t), out)
         return np.array(list(out))
+
+
+def numflux(params: dict, wi, wo, hb, nx, ny):
+    lib = _lib()
+    prm = make_params(params)
+    a, b = np.ascontiguousarray(wi, np.float64), np.ascontiguousarray(wo, np.float64)
+    out = np.zeros(3)
+    lib.orc_numflux(C.byref(prm), _ptr(a), _ptr(b), float(hb), float(nx), float(ny), _ptr(out))
+    return out
 
 
 def basis(p: int, xi: float, eta: float):

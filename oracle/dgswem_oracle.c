@@ -26,7 +26,9 @@
  *     a minus);
  *   - the pressure flux is (g/2)(H^2 - h_b^2) (the flux matrix of Sec. 2.2 drops
  *     the 1/2; Eq. SWE and Sec. 5.2.1 keep it), written as (g/2) zeta (zeta + 2 h_b);
- *   - numerical flux: local Lax-Friedrichs (Sec. 2.2 allows LLF or Roe);
+ *   - numerical flux: local Lax-Friedrichs, or Roe (Sec. 2.2 names both): Roe-averaged depth
+ *     (H_i + H_o)/2 and sqrt(H)-weighted velocity, |A| from its eigen-decomposition in the edge
+ *     frame, Harten's entropy fix on the two acoustic waves with delta = c/10;
  *   - "Gauss-Lobatto quadrature": a triangle needs a 2D rule; area integrals use
  *     Dunavant's symmetric rules (degree 4, 6 points for p=1; degree 6, 12 points
  *     for p=2) and edges Gauss-Legendre (2 points for p=1, 4 for p=2);
@@ -43,7 +45,9 @@
  *     modes of each variable; wet/dry: mean-preserving vertex-depth fix (Bunya et
  *     al. 2009 style), see wetdry() below;
  *   - land boundary: mirror ghost state; open boundary: zeta = A sin(2 pi t/T + phi),
- *     q taken from the interior;
+ *     q taken from the interior; river boundary (Gamma_river, named in Sec. 2.1): the land mirror
+ *     shifted so that the mean normal discharge of the two traces is the inflow -q_in;
+ *   - rain R (Eq. SWE): a uniform rate in the continuity equation;
  *   - hurricane: Holland (1980) pressure and gradient wind, Garratt (1977) drag.
  * Parity unpinned: slope limiter and wet/dry (pinned only by invariants).
  *
@@ -75,6 +79,9 @@ typedef struct {
   int32_t rk_scheme; /* 0 SSP(2,2), 1 SSP(3,3), 2 SSP(3,2), 3 SSP(4,2), 4 SSP(5,2), 5 SSP(4,3), 6 custom */
   int32_t rk_stages; /* custom: number of stages */
   double rk_coeffs[24]; /* custom: (a_i, b_i, c_i) per stage */
+  int32_t flux;         /* 0 local Lax-Friedrichs, 1 Roe */
+  double rain_rate;     /* R of Eq. SWE, uniform (m/s) */
+  double river_q;       /* inflow discharge per unit width on river edges (m^2/s) */
 } orc_params;
 
 typedef void (*orc_field_cb)(double t, int32_t n, const double *xy, double *out);
@@ -500,11 +507,64 @@ static void llf(double g, const double wi[3], const double wo[3], double hb, dou
   for (int v = 0; v < 3; ++v) out[v] = 0.5 * (Fi[v] + Fo[v]) - 0.5 * lam * (wo[v] - wi[v]);
 }
 
-/* land boundary: mirror ghost zeta- = zeta+, q- = q+ - 2 (q+.n) n, then LLF */
-static void wall_flux(double g, const double wi[3], double hb, double nx, double ny, double out[3]) {
+/* Roe (1981) flux, n from the inner (wi) to the outer (wo) state.  In the edge frame (normal n,
+ * tangent t = (-ny, nx)) the state is (H, q_n, q_t); the Roe averages are H~ = (Hi + Ho)/2,
+ * u~ = (sqrt(Hi) ui + sqrt(Ho) uo) / (sqrt(Hi) + sqrt(Ho)) (both components), c~ = sqrt(g H~); the
+ * eigenvalues u~_n - c~, u~_n, u~_n + c~ have right eigenvectors (1, u~_n - c~, u~_t),
+ * (0, 0, 1), (1, u~_n + c~, u~_t) and wave strengths
+ * a1 = ((u~_n + c~) dH - dq_n) / (2 c~), a2 = dq_t - u~_t dH, a3 = (dq_n - (u~_n - c~) dH) / (2 c~);
+ * Fhat = (F(wi) + F(wo)).n / 2 - sum_k |lambda_k| a_k r_k / 2, with |lambda| of the acoustic waves
+ * replaced by (lambda^2 + d^2) / (2 d) below d = c~/10 (Harten).  dH = d zeta (h_b continuous). */
+static double harten(double lam, double d) {
+  double a = fabs(lam);
+  return (a < d) ? 0.5 * (lam * lam + d * d) / d : a;
+}
+
+static void roe(double g, const double wi[3], const double wo[3], double hb, double nx, double ny, double out[3]) {
+  double Fi[3], Fo[3];
+  flux_n(g, wi, hb, nx, ny, Fi);
+  flux_n(g, wo, hb, nx, ny, Fo);
+  double Hi = wi[0] + hb, Ho = wo[0] + hb;
+  double qni = wi[1] * nx + wi[2] * ny, qti = -wi[1] * ny + wi[2] * nx;
+  double qno = wo[1] * nx + wo[2] * ny, qto = -wo[1] * ny + wo[2] * nx;
+  double si = sqrt(Hi > 0.0 ? Hi : 0.0), so = sqrt(Ho > 0.0 ? Ho : 0.0);
+  double un = 0.0, ut = 0.0;
+  if (si + so > 0.0) {
+    un = (si * (Hi > 0.0 ? qni / Hi : 0.0) + so * (Ho > 0.0 ? qno / Ho : 0.0)) / (si + so);
+    ut = (si * (Hi > 0.0 ? qti / Hi : 0.0) + so * (Ho > 0.0 ? qto / Ho : 0.0)) / (si + so);
+  }
+  double Hm = 0.5 * (Hi + Ho);
+  double c = sqrt(g * (Hm > 0.0 ? Hm : 0.0));
+  double dH = wo[0] - wi[0], dqn = qno - qni, dqt = qto - qti;
+  double dn = 0.0, dt = 0.0, dh = 0.0; /* |A| dw in the edge frame */
+  if (c > 0.0) {
+    double a1 = ((un + c) * dH - dqn) / (2.0 * c);
+    double a3 = (dqn - (un - c) * dH) / (2.0 * c);
+    double a2 = dqt - ut * dH;
+    double l1 = harten(un - c, 0.1 * c), l2 = fabs(un), l3 = harten(un + c, 0.1 * c);
+    dh = l1 * a1 + l3 * a3;
+    dn = l1 * a1 * (un - c) + l3 * a3 * (un + c);
+    dt = l1 * a1 * ut + l2 * a2 + l3 * a3 * ut;
+  }
+  out[0] = 0.5 * (Fi[0] + Fo[0]) - 0.5 * dh;
+  out[1] = 0.5 * (Fi[1] + Fo[1]) - 0.5 * (dn * nx - dt * ny);
+  out[2] = 0.5 * (Fi[2] + Fo[2]) - 0.5 * (dn * ny + dt * nx);
+}
+
+/* the numerical flux selected by the parameters */
+static void num_flux(const orc_params *P, const double wi[3], const double wo[3], double hb, double nx, double ny,
+                     double out[3]) {
+  if (P->flux == 1)
+    roe(P->g, wi, wo, hb, nx, ny, out);
+  else
+    llf(P->g, wi, wo, hb, nx, ny, out);
+}
+
+/* land boundary: mirror ghost zeta- = zeta+, q- = q+ - 2 (q+.n) n, then the numerical flux */
+static void wall_flux(const orc_params *P, const double wi[3], double hb, double nx, double ny, double out[3]) {
   double qn = wi[1] * nx + wi[2] * ny;
   double wo[3] = {wi[0], wi[1] - 2.0 * qn * nx, wi[2] - 2.0 * qn * ny};
-  llf(g, wi, wo, hb, nx, ny, out);
+  num_flux(P, wi, wo, hb, nx, ny, out);
 }
 
 /* ------------------------------------------------------ AREA (Alg. 1) */
@@ -554,7 +614,7 @@ static void area_integrals(orc *o, int irk) {
       double Gx = qx * qx / H + Pp, Gy = qx * qy / H;
       double Hx = qx * qy / H, Hy = qy * qy / H + Pp;
       /* Continuity_Source, X_Source, Y_Source */
-      double SR = 0.0;
+      double SR = P->rain_rate;
       double tau = friction_tau(P, qx, qy, H);
       double Sx = P->g * ze * dhb_dx - tau * qx + f * qy;
       double Sy = P->g * ze * dhb_dy - tau * qy - f * qx;
@@ -646,14 +706,14 @@ static void edge_integrals(orc *o, int irk, double ts) {
       double wlen = 0.5 * o->ELEN[L] * o->WE[i];
       if (flows) {
         double F[3], Fm[3];
-        llf(P->g, wp, wm, hb, nx, ny, F);
+        num_flux(P, wp, wm, hb, nx, ny, F);
         add_slot(o, ep, lp, i, wlen, F);
         for (int v = 0; v < 3; ++v) Fm[v] = -F[v]; /* n(e-) = -n(e+) */
         add_slot(o, em, lm, im, wlen, Fm);
       } else {
         double Fp[3], Fm[3];
-        wall_flux(P->g, wp, hb, nx, ny, Fp);
-        wall_flux(P->g, wm, hb, -nx, -ny, Fm);
+        wall_flux(P, wp, hb, nx, ny, Fp);
+        wall_flux(P, wm, hb, -nx, -ny, Fm);
         add_slot(o, ep, lp, i, wlen, Fp);
         add_slot(o, em, lm, im, wlen, Fm);
       }
@@ -669,17 +729,22 @@ static void edge_integrals(orc *o, int irk, double ts) {
       double wp[3], F[3], hb = edge_hb(o, L, i);
       trace(o, irk, ep, lp, i, wp);
       if (o->transmissive) {
-        llf(P->g, wp, wp, hb, nx, ny, F);
+        num_flux(P, wp, wp, hb, nx, ny, F);
       } else if (o->mms_bnd) {
         int bi = -1;
         for (int b = 0; b < o->nbnd; ++b)
           if (o->BLIST[b] == L) { bi = b; break; }
-        llf(P->g, wp, o->BVAL + ((size_t)bi * nq + i) * 3, hb, nx, ny, F);
+        num_flux(P, wp, o->BVAL + ((size_t)bi * nq + i) * 3, hb, nx, ny, F);
       } else if (o->ETYPE[L] == 1) {
         double wo[3] = {zt, wp[1], wp[2]};
-        llf(P->g, wp, wo, hb, nx, ny, F);
+        num_flux(P, wp, wo, hb, nx, ny, F);
+      } else if (o->ETYPE[L] == 2) {
+        /* river: q- = q+ - 2 (q+.n + q_in) n, so that (q+ + q-).n / 2 = -q_in */
+        double qn = wp[1] * nx + wp[2] * ny;
+        double wo[3] = {wp[0], wp[1] - 2.0 * (qn + P->river_q) * nx, wp[2] - 2.0 * (qn + P->river_q) * ny};
+        num_flux(P, wp, wo, hb, nx, ny, F);
       } else {
-        wall_flux(P->g, wp, hb, nx, ny, F);
+        wall_flux(P, wp, hb, nx, ny, F);
       }
       add_slot(o, ep, lp, i, 0.5 * o->ELEN[L] * o->WE[i], F);
     }
@@ -1091,6 +1156,12 @@ void orc_forcing(orc *o, double t, double *out) {
   memcpy(out, o->TSX, sizeof(double) * o->nn);
   memcpy(out + o->nn, o->TSY, sizeof(double) * o->nn);
   memcpy(out + 2 * (size_t)o->nn, o->PA, sizeof(double) * o->nn);
+}
+
+/* the point numerical flux, for checking its properties directly */
+void orc_numflux(const orc_params *P, const double *wi, const double *wo, double hb, double nx, double ny,
+                 double *out) {
+  num_flux(P, wi, wo, hb, nx, ny, out);
 }
 
 /* reference tables, for checking against closed forms */

@@ -49,6 +49,8 @@ int check_params(const dgswem_params *p, std::string &msg) {
       msg = "params: hurricane needs rho_air, rho_water, rmax_m, holland_b > 0"; return DGSWEM_EINVAL;
     }
   }
+  if (p->flux != DGSWEM_FLUX_LLF && p->flux != DGSWEM_FLUX_ROE) { msg = "params: unknown numerical flux"; return DGSWEM_EINVAL; }
+  if (!std::isfinite(p->rain_rate) || !std::isfinite(p->river_q)) { msg = "params: non-finite rain or river rate"; return DGSWEM_EINVAL; }
   double a[MAX_STAGES], b[MAX_STAGES], c[MAX_STAGES], tau[MAX_STAGES];
   if (rk_stage_table(*p, a, b, c, tau) < 2) { msg = "params: unknown Runge-Kutta scheme or bad table"; return DGSWEM_EINVAL; }
   return 0;
@@ -86,6 +88,9 @@ Phys make_phys(const dgswem_params &p) {
   ph.wetdry = p.h0 > 0.0 ? 1 : 0;
   ph.limiter = p.limiter ? 1 : 0;
   ph.hurricane = p.hurricane ? 1 : 0;
+  ph.flux = p.flux;
+  ph.rain = p.rain_rate;
+  ph.river_q = p.river_q;
   return ph;
 }
 

@@ -30,6 +30,7 @@ enum {
 
 constexpr int NBR_LAND = -1;
 constexpr int NBR_OPEN = -2;
+constexpr int NBR_RIVER = -3;
 
 // Mesh after preprocessing, elements in internal (locality) order.
 struct HostMesh {
@@ -79,7 +80,8 @@ struct Phys {
   double pc, pn, rmax, hB, vt, x0, y0, heading, flat, rho_air, rho_w;
   double cos_h, sin_h;     // heading direction of the storm track
   double hB_rho_air, rho_ratio, inv_rho_w;  // B / rho_air, rho_air / rho_w, 1 / rho_w
-  int friction, wetdry, limiter, hurricane;
+  int friction, wetdry, limiter, hurricane, flux;
+  double rain, river_q;
 };
 
 struct DevMesh {

@@ -113,12 +113,81 @@ __device__ __forceinline__ void llf(T g, T sqrt_g, const T wi[3], const T wo[3],
   for (int v = 0; v < 3; ++v) out[v] = T(0.5) * (a.F[v] + b.F[v]) - T(0.5) * lam * (wo[v] - wi[v]);
 }
 
-// Land (no normal flow): mirror ghost zeta- = zeta+, q- = q+ - 2 (q+.n) n, then LLF.
+// Roe (1981) flux, n from wi to wo.  Edge frame (n, t = (-ny, nx)), state (H, q_n, q_t); Roe
+// averages H~ = (Hi + Ho)/2, u~ = sqrt(H)-weighted mean velocity, c~ = sqrt(g H~); eigenvalues
+// u~_n -+ c~ (acoustic, Harten entropy fix with delta = c~/10) and u~_n (shear); wave strengths
+// a1 = ((u~_n + c~) dH - dq_n)/(2c~), a2 = dq_t - u~_t dH, a3 = (dq_n - (u~_n - c~) dH)/(2c~);
+// Fhat = (F(wi) + F(wo)).n / 2 - |A~| dw / 2.  dH = d zeta because h_b is continuous.
 template <typename T>
-__device__ __forceinline__ void wall(T g, T sqrt_g, const T wi[3], T hb, T nx, T ny, T out[3]) {
+__device__ __forceinline__ T harten(T lam, T d) {
+  const T a = fabs(lam);
+  return a < d ? T(0.5) * (lam * lam + d * d) / d : a;
+}
+
+template <typename T>
+__device__ __forceinline__ void roe(T g, const T wi[3], const T wo[3], T hb, T nx, T ny, T out[3]) {
+  const T Hi = wi[0] + hb, Ho = wo[0] + hb;
+  const T qni = wi[1] * nx + wi[2] * ny, qti = -wi[1] * ny + wi[2] * nx;
+  const T qno = wo[1] * nx + wo[2] * ny, qto = -wo[1] * ny + wo[2] * nx;
+  const T Pi = T(0.5) * g * wi[0] * (wi[0] + T(2) * hb), Po = T(0.5) * g * wo[0] * (wo[0] + T(2) * hb);
+  const T iHi = Hi > T(0) ? T(1) / Hi : T(0), iHo = Ho > T(0) ? T(1) / Ho : T(0);
+  const T uni = qni * iHi, uno = qno * iHo;
+  // F(w).n in the x/y frame: (q_n, q_x u_n + P n_x, q_y u_n + P n_y)
+  const T Fi[3] = {qni, wi[1] * uni + Pi * nx, wi[2] * uni + Pi * ny};
+  const T Fo[3] = {qno, wo[1] * uno + Po * nx, wo[2] * uno + Po * ny};
+  const T si = sqrt(Hi > T(0) ? Hi : T(0)), so = sqrt(Ho > T(0) ? Ho : T(0));
+  T un = T(0), ut = T(0);
+  if (si + so > T(0)) {
+    const T inv = T(1) / (si + so);
+    un = (si * uni + so * uno) * inv;
+    ut = (si * (qti * iHi) + so * (qto * iHo)) * inv;
+  }
+  const T Hm = T(0.5) * (Hi + Ho);
+  const T c = sqrt(g * (Hm > T(0) ? Hm : T(0)));
+  const T dH = wo[0] - wi[0], dqn = qno - qni, dqt = qto - qti;
+  T dh = T(0), dn = T(0), dt = T(0);
+  if (c > T(0)) {
+    const T i2c = T(0.5) / c;
+    const T a1 = ((un + c) * dH - dqn) * i2c;
+    const T a3 = (dqn - (un - c) * dH) * i2c;
+    const T a2 = dqt - ut * dH;
+    const T l1 = harten(un - c, T(0.1) * c), l2 = fabs(un), l3 = harten(un + c, T(0.1) * c);
+    dh = l1 * a1 + l3 * a3;
+    dn = l1 * a1 * (un - c) + l3 * a3 * (un + c);
+    dt = l1 * a1 * ut + l2 * a2 + l3 * a3 * ut;
+  }
+  out[0] = T(0.5) * (Fi[0] + Fo[0]) - T(0.5) * dh;
+  out[1] = T(0.5) * (Fi[1] + Fo[1]) - T(0.5) * (dn * nx - dt * ny);
+  out[2] = T(0.5) * (Fi[2] + Fo[2]) - T(0.5) * (dn * ny + dt * nx);
+}
+
+// River inflow: the land mirror shifted so that (q+ + q-).n / 2 = -q_in, then the numerical flux.
+template <typename T>
+__device__ __forceinline__ void river(const Phys &ph, T g, T sqrt_g, const T wi[3], T hb, T nx, T ny, T out[3]);
+
+// The numerical flux selected by the parameters (uniform branch).
+template <typename T>
+__device__ __forceinline__ void numflux(const Phys &ph, T g, T sqrt_g, const T wi[3], const T wo[3], T hb, T nx,
+                                        T ny, T out[3]) {
+  if (ph.flux == DGSWEM_FLUX_ROE)
+    roe(g, wi, wo, hb, nx, ny, out);
+  else
+    llf(g, sqrt_g, wi, wo, hb, nx, ny, out);
+}
+
+template <typename T>
+__device__ __forceinline__ void river(const Phys &ph, T g, T sqrt_g, const T wi[3], T hb, T nx, T ny, T out[3]) {
+  const T d = T(2) * (wi[1] * nx + wi[2] * ny + (T)ph.river_q);
+  const T wo[3] = {wi[0], wi[1] - d * nx, wi[2] - d * ny};
+  numflux(ph, g, sqrt_g, wi, wo, hb, nx, ny, out);
+}
+
+// Land (no normal flow): mirror ghost zeta- = zeta+, q- = q+ - 2 (q+.n) n, then the numerical flux.
+template <typename T>
+__device__ __forceinline__ void wall(const Phys &ph, T g, T sqrt_g, const T wi[3], T hb, T nx, T ny, T out[3]) {
   const T qn = wi[1] * nx + wi[2] * ny;
   const T wo[3] = {wi[0], wi[1] - T(2) * qn * nx, wi[2] - T(2) * qn * ny};
-  llf(g, sqrt_g, wi, wo, hb, nx, ny, out);
+  numflux(ph, g, sqrt_g, wi, wo, hb, nx, ny, out);
 }
 
 template <typename T>
@@ -316,7 +385,7 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
     }
     const T hb = T(0.5) * ((T(1) - tb.se[q]) * from_d<T>(hbA) + (T(1) + tb.se[q]) * from_d<T>(hbB));
     T f[3];
-    llf(g, sqg, a, b, hb, nx, ny, f);
+    numflux(ph, g, sqg, a, b, hb, nx, ny, f);
     const T wgt = hl * tb.we[q];
 #pragma unroll
     for (int v = 0; v < 3; ++v) F[(size_t)(v * NQE + q) * nint + d] = wgt * f[v];
@@ -517,6 +586,7 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
     for (int k = 0; k < ND; ++k) {
       T L = r[v][k] * idJ * tb.inrm[k];
       if (k < 3) L += (v == 1) ? src1[k] : (v == 2 ? src2[k] : T(0));
+      if (v == 0 && k == 0) L += (T)ph.rain;  // (phi_0, R) / (|J| ||phi_0||^2) = R
       const size_t ix = (size_t)(v * ND + k) * base + e;
       const double Ld = to_d<T>(L);
       double out;
@@ -621,21 +691,24 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
               for (int k = 0; k < ND; ++k) x += wn[v][k] * s_phe[lj][NQE - 1 - q][k];
               wm[v] = x;
             }
-            llf(g, sqg, wp[q], wm, hbq[q], nx, ny, Fh[q]);
+            numflux(ph, g, sqg, wp[q], wm, hbq[q], nx, ny, Fh[q]);
           }
         }
       }
-      if (j == NBR_OPEN) {
+      if (j == NBR_RIVER) {
+#pragma unroll
+        for (int q = 0; q < NQE; ++q) river(ph, g, sqg, wp[q], hbq[q], nx, ny, Fh[q]);
+      } else if (j == NBR_OPEN) {
         const double ts = stage_time(s.clk, s.tau, s.tide_t);
         const T zt = from_d<T>(ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase));
 #pragma unroll
         for (int q = 0; q < NQE; ++q) {
           const T wo[3] = {zt, wp[q][1], wp[q][2]};
-          llf(g, sqg, wp[q], wo, hbq[q], nx, ny, Fh[q]);
+          numflux(ph, g, sqg, wp[q], wo, hbq[q], nx, ny, Fh[q]);
         }
       } else if (!flows) {  // land boundary, or an interior edge closed by wetting/drying
 #pragma unroll
-        for (int q = 0; q < NQE; ++q) wall(g, sqg, wp[q], hbq[q], nx, ny, Fh[q]);
+        for (int q = 0; q < NQE; ++q) wall(ph, g, sqg, wp[q], hbq[q], nx, ny, Fh[q]);
       }
     }
 #pragma unroll
@@ -741,7 +814,7 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
       const T wgt = hl * tb.we[q];
       if (flows) {
         T f[3];
-        llf(g, sqg, ta[q], tbq, hbq[q], nx, ny, f);
+        numflux(ph, g, sqg, ta[q], tbq, hbq[q], nx, ny, f);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
           if (ina) slot(a - e0, la, q, v) = wgt * f[v];
@@ -750,23 +823,26 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
       } else {  // closed by wetting/drying: each side sees a wall
         if (ina) {
           T f[3];
-          wall(g, sqg, ta[q], hbq[q], nx, ny, f);
+          wall(ph, g, sqg, ta[q], hbq[q], nx, ny, f);
 #pragma unroll
           for (int v = 0; v < 3; ++v) slot(a - e0, la, q, v) = wgt * f[v];
         }
         if (inb) {
           T f[3];
-          wall(g, sqg, tbq, hbq[q], -nx, -ny, f);
+          wall(ph, g, sqg, tbq, hbq[q], -nx, -ny, f);
 #pragma unroll
           for (int v = 0; v < 3; ++v) slot(b - e0, lb, NQE - 1 - q, v) = wgt * f[v];
         }
       }
     }
-  } else if (b == NBR_LAND) {
+  } else if (b == NBR_LAND || b == NBR_RIVER) {
 #pragma unroll
     for (int q = 0; q < NQE; ++q) {
       T f[3];
-      wall(g, sqg, ta[q], hbq[q], nx, ny, f);
+      if (b == NBR_RIVER)
+        river(ph, g, sqg, ta[q], hbq[q], nx, ny, f);
+      else
+        wall(ph, g, sqg, ta[q], hbq[q], nx, ny, f);
 #pragma unroll
       for (int v = 0; v < 3; ++v) slot(a - e0, la, q, v) = hl * tb.we[q] * f[v];
     }
@@ -777,7 +853,7 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
     for (int q = 0; q < NQE; ++q) {
       const T wo[3] = {zt, ta[q][1], ta[q][2]};
       T f[3];
-      llf(g, sqg, ta[q], wo, hbq[q], nx, ny, f);
+      numflux(ph, g, sqg, ta[q], wo, hbq[q], nx, ny, f);
 #pragma unroll
       for (int v = 0; v < 3; ++v) slot(a - e0, la, q, v) = hl * tb.we[q] * f[v];
     }

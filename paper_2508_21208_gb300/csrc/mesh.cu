@@ -145,7 +145,7 @@ int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, Hos
       return DGSWEM_EMESH;
     }
     int ty = m.bedge_type[i];
-    if (ty != DGSWEM_BC_LAND && ty != DGSWEM_BC_OPEN) {
+    if (ty != DGSWEM_BC_LAND && ty != DGSWEM_BC_OPEN && ty != DGSWEM_BC_RIVER) {
       msg = "mesh: unknown boundary type at boundary edge " + std::to_string(i);
       return DGSWEM_EINVAL;
     }
@@ -190,7 +190,7 @@ int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, Hos
         ty = it->type;
         bused[it - bk.begin()] = 1;
       }
-      H.nbr[(size_t)P.l * ne + P.e] = (ty == DGSWEM_BC_OPEN) ? NBR_OPEN : NBR_LAND;
+      H.nbr[(size_t)P.l * ne + P.e] = (ty == DGSWEM_BC_OPEN) ? NBR_OPEN : (ty == DGSWEM_BC_RIVER ? NBR_RIVER : NBR_LAND);
     }
     i = j;
   }

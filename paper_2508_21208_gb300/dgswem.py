@@ -19,6 +19,7 @@ ERRORS = {-1: "EINVAL", -2: "EMESH", -3: "ECUDA", -4: "ENONFINITE", -5: "ENEGDEP
           -7: "ENOMEM", -8: "ESTATE", -9: "ETOOBIG"}
 VARIANT_AUTO, VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED = 0, 1, 2, 3
 ENSEMBLE_PERSISTENT, ENSEMBLE_PHASED = 1, 2
+FLUX_LLF, FLUX_ROE = 0, 1
 FP64, FP32_MIXED = 0, 1
 
 
@@ -44,7 +45,8 @@ class Params(C.Structure):
                 ("holland_b", C.c_double), ("vt_ms", C.c_double), ("track_x0", C.c_double),
                 ("track_y0", C.c_double), ("track_heading", C.c_double), ("rho_air", C.c_double),
                 ("rho_water", C.c_double), ("rk_scheme", C.c_int32), ("rk_stages", C.c_int32),
-                ("rk_coeffs", C.c_double * 24)]
+                ("rk_coeffs", C.c_double * 24), ("flux", C.c_int32), ("rain_rate", C.c_double),
+                ("river_q", C.c_double)]
 
 
 class Tuning(C.Structure):

@@ -30,6 +30,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 # boundary edge type codes shared by both sides (an interface value, not arithmetic)
 BC_LAND = 0
 BC_OPEN = 1
+BC_RIVER = 2
 
 FRICTION_NONE = 0
 FRICTION_MANNING = 1
@@ -40,6 +41,9 @@ FP32_MIXED = 1
 
 # SSP Runge-Kutta schemes (interface codes shared by both sides)
 RK_SSP22, RK_SSP33, RK_SSP32, RK_SSP42, RK_SSP52, RK_SSP43, RK_CUSTOM = range(7)
+
+# numerical fluxes
+FLUX_LLF, FLUX_ROE = 0, 1
 
 
 def splitmix64(counter: np.ndarray) -> np.ndarray:
@@ -75,12 +79,13 @@ class Mesh:
 
 
 def grid_mesh(nx: int, ny: int, lx: float, ly: float, seed: int, jitter: float = 0.0,
-              open_sides=(), flip=None) -> Mesh:
+              open_sides=(), flip=None, river_sides=()) -> Mesh:
     """nx-by-ny squares on [0,lx]x[0,ly], each split along a seeded-random diagonal.
 
     Interior vertices are moved by up to `jitter` times the cell size in each
     coordinate (uniform in a square).  Boundary edges on the sides listed in
-    `open_sides` (any of 'left', 'right', 'bottom', 'top') are open, the rest land.
+    `open_sides` (any of 'left', 'right', 'bottom', 'top') are open, those on `river_sides` river
+    inflow edges, the rest land.
     Node (i, j) has index j*(nx+1)+i; triangles are counter-clockwise.  `flip`
     (optional, [ny, nx] bool) fixes the diagonal of each cell instead of the seed.
     """
@@ -120,7 +125,8 @@ def grid_mesh(nx: int, ny: int, lx: float, ly: float, seed: int, jitter: float =
 
     def side(name, pairs):
         edges.append(pairs)
-        types.append(np.full(len(pairs), BC_OPEN if name in open_sides else BC_LAND, np.int32))
+        code = BC_OPEN if name in open_sides else (BC_RIVER if name in river_sides else BC_LAND)
+        types.append(np.full(len(pairs), code, np.int32))
 
     ib = np.arange(nx)
     side("bottom", np.stack([ib, ib + 1], 1))
@@ -168,7 +174,8 @@ def default_params(**kw) -> dict:
              tide_amp=0.0, tide_period=44714.0, tide_phase=0.0,
              hurricane=0, pc_hpa=950.0, pn_hpa=1013.0, rmax_m=40000.0, holland_b=1.5,
              vt_ms=5.0, track_x0=0.0, track_y0=0.0, track_heading=0.0,
-             rho_air=1.15, rho_water=1000.0, rk_scheme=0, rk_stages=0, rk_coeffs=None)
+             rho_air=1.15, rho_water=1000.0, rk_scheme=0, rk_stages=0, rk_coeffs=None, flux=0,
+             rain_rate=0.0, river_q=0.0)
     for k, v in kw.items():
         if k not in p:
             raise KeyError(k)

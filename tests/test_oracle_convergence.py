@@ -50,7 +50,7 @@ def _exact():
 WF, SF, HBF = _exact()
 
 
-def _error(p, n, T=0.2):
+def _error(p, n, T=0.2, flux=0):
     mesh = synth.grid_mesh(n, n, 1.0, 1.0, 11)
     hb = HBF(mesh.xy[:, 0], mesh.xy[:, 1])
     h = 1.0 / n
@@ -58,7 +58,7 @@ def _error(p, n, T=0.2):
     nsteps = int(math.ceil(T / dt))
     dt = T / nsteps
     prm = synth.default_params(p=p, g=G, dt=dt, friction=synth.FRICTION_QUADRATIC, cf=CF,
-                               coriolis=1, coriolis_lat_deg=LAT)
+                               coriolis=1, coriolis_lat_deg=LAT, flux=flux)
     o = oracle.Oracle(mesh, hb, prm)
     o.project(WF, 0.0)
     o.set_mms(SF, WF)
@@ -66,10 +66,11 @@ def _error(p, n, T=0.2):
     return o.l2err(WF, T)
 
 
+@pytest.mark.parametrize("flux", [synth.FLUX_LLF, synth.FLUX_ROE])
 @pytest.mark.parametrize("p", [1, 2])
-def test_convergence_rate(p):
+def test_convergence_rate(p, flux):
     ns = [4, 8, 16, 32]
-    errs = np.array([_error(p, n) for n in ns])
+    errs = np.array([_error(p, n, flux=flux) for n in ns])
     rates = np.log2(errs[:-1] / errs[1:])
     # the finest two refinements must show the asymptotic rate p+1 in every variable
     assert np.all(rates[-1] > p + 1 - 0.25), (errs, rates)
