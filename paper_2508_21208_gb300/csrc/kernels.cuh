@@ -1248,9 +1248,11 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
 }
 
 // One time step of every member in one cooperative launch: per stage, WIND -> element update ->
-// limiter/wet-dry over the flat tile lists, separated by bounded grid barriers.
+// limiter/wet-dry over the flat tile lists, separated by bounded grid barriers.  The float form is
+// held to 3 (p = 1) or 2 (p = 2) resident 256-thread blocks per SM: left free, the union of the
+// phases takes more registers than any phase needs and only 2 blocks fit.
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_ens_persistent(const EnsArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 3 : 2) : 1)) k_ens_persistent(const EnsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   __shared__ MemberDev sd;
