@@ -111,7 +111,7 @@ typedef struct {
   /* state: U[(irk*3 + var)*nd + k][e]; irk 0 = u^n, 1 = u^(1) */
   double *U, *RHS, *EDGE; /* EDGE[((var*ne + e)*3 + l)*nd + k] */
   unsigned char *WD;      /* 0 wet, 1 partially wet, 2 dry */
-  double *TSX, *TSY, *PA; /* nodal wind stress / rho_w and pressure / rho_w */
+  double *TSX, *TSY, *PA; /* nodal wind stress / rho_w and pressure anomaly (p - pn) / rho_w */
   double *MEAN;           /* scratch: element means used by the limiter */
   double dt, t0;
   int64_t nstep;
@@ -443,7 +443,10 @@ static int wetdry_on(const orc *o) { return o->prm.h0 > 0.0; }
 /* Holland (1980) parametric vortex: p(r) = pc + (pn - pc) exp(-(Rmax/r)^B), gradient wind
  * V = sqrt(B/rho_a (pn-pc) (Rmax/r)^B exp(-(Rmax/r)^B) + (r f/2)^2) - r f/2, surface wind 0.9 V,
  * counter-clockwise, plus half the translation velocity; Garratt (1977) drag
- * C_d = min(0.75 + 0.067 |U|, 3.5) 1e-3; stress / rho_w = rho_a/rho_w C_d |U| U. */
+ * C_d = min(0.75 + 0.067 |U|, 3.5) 1e-3; stress / rho_w = rho_a/rho_w C_d |U| U.
+ * The pressure enters Eq. SWE only through its gradient, so the stored value is the anomaly
+ * p - pn = (pn - pc) expm1(-(Rmax/r)^B): the same gradient, without the cancellation of
+ * differencing values near pn (about 1e5 Pa) across an element. */
 static void wind(orc *o, double t) {
   const orc_params *P = &o->prm;
   double f = 2.0 * 7.2921e-5 * sin(P->coriolis_lat_deg * M_PI / 180.0);
@@ -456,12 +459,12 @@ static void wind(orc *o, double t) {
     double r = sqrt(dx * dx + dy * dy);
     double pr, ux, uy;
     if (r < 1.0) {
-      pr = pc;
+      pr = pc - pn;
       ux = 0.5 * P->vt_ms * cos(P->track_heading);
       uy = 0.5 * P->vt_ms * sin(P->track_heading);
     } else {
       double A = pow(P->rmax_m / r, B), E = exp(-A);
-      pr = pc + (pn - pc) * E;
+      pr = (pn - pc) * expm1(-A);
       double V = sqrt(B / P->rho_air * (pn - pc) * A * E + (0.5 * r * f) * (0.5 * r * f)) - 0.5 * r * f;
       ux = 0.9 * V * (-dy / r) + 0.5 * P->vt_ms * cos(P->track_heading);
       uy = 0.9 * V * (dx / r) + 0.5 * P->vt_ms * sin(P->track_heading);
@@ -1150,7 +1153,7 @@ void orc_apply_wetdry(orc *o) { wetdry(o, 0); }
 
 void orc_flags(const orc *o, unsigned char *out) { memcpy(out, o->WD, o->ne); }
 
-/* nodal forcing at time t: out is [3][nn] = (tau_x/rho_w, tau_y/rho_w, p_a/rho_w) */
+/* nodal forcing at time t: out is [3][nn] = (tau_x/rho_w, tau_y/rho_w, (p_a - p_n)/rho_w) */
 void orc_forcing(orc *o, double t, double *out) {
   wind(o, t);
   memcpy(out, o->TSX, sizeof(double) * o->nn);

@@ -70,6 +70,86 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
 }
 
+// ------------------------------------------------------------------------ FP64 reciprocal and roots
+// The FP64 form is bound by GB300's FP64 pipe, where an IEEE divide or square root costs about ten
+// instructions.  These take a float seed from the special-function unit (a separate pipe) and
+// finish with one third-order correction in double (Newton-Raphson carried to the second-order
+// term of the binomial series, i.e. Householder's method of order 3):
+//   1/x:        y0 ~ 1/x,        e = 1 - x y0,    1/x       = y0 (1 + e + e^2)          + O(e^3)
+//   1/sqrt(x):  y0 ~ 1/sqrt(x),  e = 1 - x y0^2,  1/sqrt(x) = y0 (1 + e/2 + 3e^2/8)    + O(e^3)
+//   sqrt(x)   = (x y0) (1 + e/2 + 3e^2/8)                                              + O(e^3)
+// The seed reads x's sign, exponent and top 20 mantissa bits (relative error < 2^-20) and the
+// approximate MUFU result adds < 2^-22, so |e| < 2^-18 and the truncation error is below 2^-54:
+// three (reciprocal) or five (roots) FP64 instructions, results within about an ulp of the
+// correctly rounded value.  |x| outside [2^-100, 2^101) (zero, subnormals, infinity, NaN), or a
+// negative operand of a root, takes the IEEE operation.
+__device__ __forceinline__ bool seed_range(int hi) {
+  return (unsigned)(((hi >> 20) & 0x7ff) - 923) <= 200u;
+}
+__device__ __forceinline__ float seed_float(int hi) {
+  return __int_as_float((hi & (int)0x80000000) | ((((hi >> 20) & 0x7ff) - 896) << 23) | ((hi & 0xfffff) << 3));
+}
+// exact widening of a normal float (the seeds are normal by construction)
+__device__ __forceinline__ double widen_normal(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned hi = (u & 0x80000000u) | ((((u >> 23) & 0xffu) + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 0x7u) << 29));
+}
+__device__ __forceinline__ double rcp_d(double x) {
+  const int hi = __double2hiint(x);
+  if (!seed_range(hi)) return 1.0 / x;
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(seed_float(hi)));
+  const double y0 = widen_normal(yf);
+  const double e = fma(-x, y0, 1.0);
+  return fma(y0, fma(e, e, e), y0);
+}
+__device__ __forceinline__ double rsqrt_d(double x) {
+  const int hi = __double2hiint(x);
+  if (hi < 0 || !seed_range(hi)) return rsqrt(x);
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(seed_float(hi)));
+  const double y0 = widen_normal(yf);
+  const double e = fma(-(x * y0), y0, 1.0);
+  return fma(y0 * e, fma(0.375, e, 0.5), y0);
+}
+__device__ __forceinline__ double sqrt_d(double x) {
+  const int hi = __double2hiint(x);
+  if (hi < 0 || !seed_range(hi)) return sqrt(x);
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(seed_float(hi)));
+  const double y0 = widen_normal(yf);
+  const double a = x * y0;
+  const double e = fma(-a, y0, 1.0);
+  return fma(a * e, fma(0.375, e, 0.5), a);
+}
+// the float form keeps the plain operations (its pipe is not the bound)
+template <typename T>
+__device__ __forceinline__ T rcp_t(T x) { return T(1) / x; }
+template <>
+__device__ __forceinline__ double rcp_t<double>(double x) { return rcp_d(x); }
+template <typename T>
+__device__ __forceinline__ T sqrt_t(T x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ double sqrt_t<double>(double x) { return sqrt_d(x); }
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt_d(x); }
+// x > 0 from the bits (an integer compare; positive NaN counts as positive and stays non-finite)
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool positive(float x) { return __float_as_int(x) > 0; }
+
+// Value of a modal expansion at a point: the Dubiner mode psi_00 is identically 1 (Eq. dubiner),
+// so its coefficient enters without a multiply.
+template <int ND, typename T>
+__device__ __forceinline__ T modal_value(const T (&w)[ND], const T *ph) {
+  T x = w[0];
+#pragma unroll
+  for (int k = 1; k < ND; ++k) x += w[k] * ph[k];
+  return x;
+}
+
 // ------------------------------------------------------------------------ point physics
 // Normal flux F(w).n of Eq. SWE with the pressure term (g/2)(H^2 - h_b^2) = (g/2) zeta (zeta + 2 h_b).
 template <typename T>
@@ -78,16 +158,15 @@ struct Side {
   T s;     // |u.n| + sqrt(g H)
 };
 
-// 1/H and sqrt(g H) come from one reciprocal square root (a divide and a square root cost about
-// ten FP64-pipe instructions each on GB300); H <= 0 falls back to a plain divide.
+// 1/H and sqrt(g H) come from one reciprocal square root; H <= 0 falls back to a plain divide.
 template <typename T>
 __device__ __forceinline__ Side<T> side_flux(T g, T sqrt_g, const T w[3], T hb, T nx, T ny) {
   Side<T> r;
   const T H = w[0] + hb;
   const T qn = w[1] * nx + w[2] * ny;
   T iH, c;
-  if (H > T(0)) {
-    const T rs = rsqrt(H);
+  if (positive(H)) {
+    const T rs = rsqrt_t(H);
     iH = rs * rs;
     c = sqrt_g * H * rs;
   } else {
@@ -130,24 +209,24 @@ __device__ __forceinline__ void roe(T g, const T wi[3], const T wo[3], T hb, T n
   const T qni = wi[1] * nx + wi[2] * ny, qti = -wi[1] * ny + wi[2] * nx;
   const T qno = wo[1] * nx + wo[2] * ny, qto = -wo[1] * ny + wo[2] * nx;
   const T Pi = T(0.5) * g * wi[0] * (wi[0] + T(2) * hb), Po = T(0.5) * g * wo[0] * (wo[0] + T(2) * hb);
-  const T iHi = Hi > T(0) ? T(1) / Hi : T(0), iHo = Ho > T(0) ? T(1) / Ho : T(0);
+  const T iHi = positive(Hi) ? rcp_t(Hi) : T(0), iHo = positive(Ho) ? rcp_t(Ho) : T(0);
   const T uni = qni * iHi, uno = qno * iHo;
   // F(w).n in the x/y frame: (q_n, q_x u_n + P n_x, q_y u_n + P n_y)
   const T Fi[3] = {qni, wi[1] * uni + Pi * nx, wi[2] * uni + Pi * ny};
   const T Fo[3] = {qno, wo[1] * uno + Po * nx, wo[2] * uno + Po * ny};
-  const T si = sqrt(Hi > T(0) ? Hi : T(0)), so = sqrt(Ho > T(0) ? Ho : T(0));
+  const T si = positive(Hi) ? sqrt_t(Hi) : T(0), so = positive(Ho) ? sqrt_t(Ho) : T(0);
   T un = T(0), ut = T(0);
-  if (si + so > T(0)) {
-    const T inv = T(1) / (si + so);
+  if (positive(si + so)) {
+    const T inv = rcp_t(si + so);
     un = (si * uni + so * uno) * inv;
     ut = (si * (qti * iHi) + so * (qto * iHo)) * inv;
   }
   const T Hm = T(0.5) * (Hi + Ho);
-  const T c = sqrt(g * (Hm > T(0) ? Hm : T(0)));
+  const T c = positive(Hm) ? sqrt_t(g * Hm) : T(0);
   const T dH = wo[0] - wi[0], dqn = qno - qni, dqt = qto - qti;
   T dh = T(0), dn = T(0), dt = T(0);
-  if (c > T(0)) {
-    const T i2c = T(0.5) / c;
+  if (positive(c)) {
+    const T i2c = T(0.5) * rcp_t(c);
     const T a1 = ((un + c) * dH - dqn) * i2c;
     const T a3 = (dqn - (un - c) * dH) * i2c;
     const T a2 = dqt - ut * dH;
@@ -192,7 +271,7 @@ __device__ __forceinline__ void wall(const Phys &ph, T g, T sqrt_g, const T wi[3
 
 template <typename T>
 __device__ __forceinline__ T friction_tau(const Phys &ph, T qx, T qy, T H, T iH) {
-  const T qm = sqrt(qx * qx + qy * qy);
+  const T qm = sqrt_t(qx * qx + qy * qy);
   if (ph.friction == DGSWEM_FRICTION_QUADRATIC) return (T)ph.cf * qm * iH * iH;
   if (ph.friction == DGSWEM_FRICTION_MANNING) return (T)ph.gn2 * qm * iH * iH * rcbrt(H);
   return T(0);
@@ -215,9 +294,9 @@ __device__ __forceinline__ bool edge_flows(const Phys &ph, uint8_t f_self, uint8
   double zmax = -INFINITY;
 #pragma unroll
   for (int g = 0; g < NQE; ++g) {
-    double z = 0.0;
+    double z = u[ew];  // psi_00 = 1
 #pragma unroll
-    for (int k = 0; k < ND; ++k) z += u[(size_t)k * ne + ew] * td.phe[lw][g][k];
+    for (int k = 1; k < ND; ++k) z += u[(size_t)k * ne + ew] * td.phe[lw][g][k];
     zmax = z > zmax ? z : zmax;
   }
   const double bed = (-hbA > -hbB) ? -hbA : -hbB;
@@ -256,8 +335,9 @@ __device__ __forceinline__ void vortex_at(const Phys &ph, T dx, T dy, T &tx_out,
     ux = tx;
     uy = ty;
   } else {
-    const T A = pow((T)ph.rmax / r, (T)ph.hB), E = exp(-A);
-    pa = -dp + dp * E;
+    // anomaly (pn - pc) (exp(-A) - 1) from expm1: no cancellation where A is small (far field)
+    const T A = pow((T)ph.rmax / r, (T)ph.hB), em1 = expm1(-A), E = T(1) + em1;
+    pa = dp * em1;
     const T hf = T(0.5) * r * (T)ph.flat;
     const T V = sqrt((T)ph.hB_rho_air * dp * A * E + hf * hf) - hf;
     ux = T(0.9) * V * (-dy / r) + tx;
@@ -272,9 +352,9 @@ __device__ __forceinline__ void vortex_at(const Phys &ph, T dx, T dy, T &tx_out,
   pa_out = pa / (T)ph.rho_w;
 }
 
-// The mixed form's vortex: one reciprocal square root for 1/r, the hardware log2/exp2/exp
-// approximations for (Rmax/r)^B and exp(-A) (a few float ulp) and multiplications by host-computed
-// constants.  Out of line, so that every kernel that evaluates it rounds identically.
+// The mixed form's vortex: one reciprocal square root for 1/r, the hardware log2/exp2
+// approximations for (Rmax/r)^B (a few float ulp), expm1f for the pressure anomaly and
+// multiplications by host-computed constants.  Out of line, so that every kernel that evaluates it rounds identically.
 static __device__ __noinline__ void vortex_at_f(const Phys &ph, float dx, float dy, float *out) {
   const float r2 = dx * dx + dy * dy;
   const float dp = (float)(ph.pn - ph.pc);
@@ -286,8 +366,8 @@ static __device__ __noinline__ void vortex_at_f(const Phys &ph, float dx, float 
     uy = ty;
   } else {
     const float ir = rsqrtf(r2), r = r2 * ir;
-    const float A = exp2f((float)ph.hB * __log2f((float)ph.rmax * ir)), E = __expf(-A);
-    pa = -dp + dp * E;
+    const float A = exp2f((float)ph.hB * __log2f((float)ph.rmax * ir)), em1 = expm1f(-A), E = 1.f + em1;
+    pa = dp * em1;
     const float hf = 0.5f * r * (float)ph.flat;
     const float V = sqrtf((float)ph.hB_rho_air * dp * A * E + hf * hf) - hf;
     ux = 0.9f * V * (-dy * ir) + tx;
@@ -374,14 +454,8 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
     T a[3], b[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      T x = 0, y = 0;
-#pragma unroll
-      for (int k = 0; k < ND; ++k) {
-        x += wp[v][k] * s_phe[lp][q][k];
-        y += wm[v][k] * s_phe[lm][NQE - 1 - q][k];
-      }
-      a[v] = x;
-      b[v] = y;
+      a[v] = modal_value<ND, T>(wp[v], s_phe[lp][q]);
+      b[v] = modal_value<ND, T>(wm[v], s_phe[lm][NQE - 1 - q]);
     }
     const T hb = T(0.5) * ((T(1) - tb.se[q]) * from_d<T>(hbA) + (T(1) + tb.se[q]) * from_d<T>(hbB));
     T f[3];
@@ -450,16 +524,12 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
     T Gx = 0, Gy = 0, Hy = 0;  // P = 1: sums of w_q F at the points (grad phi is constant)
 #pragma unroll
     for (int q = 0; q < NQA; ++q) {
-      T z = 0, qx = 0, qy = 0;
-#pragma unroll
-      for (int k = 0; k < ND; ++k) {
-        z += w[0][k] * tb.phq[q][k];
-        qx += w[1][k] * tb.phq[q][k];
-        qy += w[2][k] * tb.phq[q][k];
-      }
+      const T z = modal_value<ND, T>(w[0], tb.phq[q]);
+      const T qx = modal_value<ND, T>(w[1], tb.phq[q]);
+      const T qy = modal_value<ND, T>(w[2], tb.phq[q]);
       const T hq = hb[0] * tb.nq[q][0] + hb[1] * tb.nq[q][1] + hb[2] * tb.nq[q][2];
       const T H = z + hq;
-      const T iH = T(1) / H;
+      const T iH = rcp_t(H);
       const T Pp = T(0.5) * g * z * (z + T(2) * hq);
       const T u = qx * iH, v = qy * iH;
       const T Fxx = qx * u + Pp, Fxy = qx * v, Fyy = qy * v + Pp;
@@ -480,10 +550,13 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
       }
       if (ph.friction) {
         const T tw = wq * friction_tau<T>(ph, qx, qy, H, iH);
+        const T tx = tw * qx, ty = tw * qy;
+        fr[0][0] += tx;  // psi_00 = 1
+        fr[1][0] += ty;
 #pragma unroll
-        for (int k = 0; k < ND; ++k) {
-          fr[0][k] += tw * qx * tb.phq[q][k];
-          fr[1][k] += tw * qy * tb.phq[q][k];
+        for (int k = 1; k < ND; ++k) {
+          fr[0][k] += tx * tb.phq[q][k];
+          fr[1][k] += ty * tb.phq[q][k];
         }
       }
     }
@@ -521,7 +594,7 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
   const T rx = c.rx, ry = c.ry, sx = c.sx, sy = c.sy, dJ = c.dJ;
   const T (&w)[3][ND] = c.w;
   const T (&hb)[3] = c.hb;
-  const T idJ = T(1) / dJ;
+  const T idJ = rcp_t(dJ);
   T src1[3] = {0, 0, 0}, src2[3] = {0, 0, 0};  // per linear mode, for q_x and q_y
   {
     const T hbx = T(0.5) * (rx * (hb[1] - hb[0]) + sx * (hb[2] - hb[0]));
@@ -553,10 +626,11 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
       const T pax = T(0.5) * (rx * (p1 - p0) + sx * (p2 - p0));
       const T pay = T(0.5) * (ry * (p1 - p0) + sy * (p2 - p0));
       // Dubiner linear modes of the interpolant through vertex values (a0, a1, a2)
-      const T hm[3] = {(hb[0] + hb[1] + hb[2]) / T(3), T(0.5) * (hb[1] - hb[0]),
-                       (T(2) * hb[2] - hb[0] - hb[1]) / T(6)};
-      const T tm[3] = {(t0 + t1 + t2) / T(3), T(0.5) * (t1 - t0), (T(2) * t2 - t0 - t1) / T(6)};
-      const T um[3] = {(u0 + u1 + u2) / T(3), T(0.5) * (u1 - u0), (T(2) * u2 - u0 - u1) / T(6)};
+      const T third = T(1) / T(3), sixth = T(1) / T(6);  // constants: no divide at run time
+      const T hm[3] = {(hb[0] + hb[1] + hb[2]) * third, T(0.5) * (hb[1] - hb[0]),
+                       (T(2) * hb[2] - hb[0] - hb[1]) * sixth};
+      const T tm[3] = {(t0 + t1 + t2) * third, T(0.5) * (t1 - t0), (T(2) * t2 - t0 - t1) * sixth};
+      const T um[3] = {(u0 + u1 + u2) * third, T(0.5) * (u1 - u0), (T(2) * u2 - u0 - u1) * sixth};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         src1[k] += tm[k] - pax * (w[0][k] + hm[k]);
@@ -664,12 +738,7 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
 #pragma unroll
       for (int q = 0; q < NQE; ++q) {
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          T x = 0;
-#pragma unroll
-          for (int k = 0; k < ND; ++k) x += w[v][k] * s_phe[l][q][k];
-          wp[q][v] = x;
-        }
+        for (int v = 0; v < 3; ++v) wp[q][v] = modal_value<ND, T>(w[v], s_phe[l][q]);
         hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hbA + (T(1) + tb.se[q]) * hbB);
       }
       bool flows = false;
@@ -685,12 +754,7 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
           for (int q = 0; q < NQE; ++q) {
             T wm[3];
 #pragma unroll
-            for (int v = 0; v < 3; ++v) {
-              T x = 0;
-#pragma unroll
-              for (int k = 0; k < ND; ++k) x += wn[v][k] * s_phe[lj][NQE - 1 - q][k];
-              wm[v] = x;
-            }
+            for (int v = 0; v < 3; ++v) wm[v] = modal_value<ND, T>(wn[v], s_phe[lj][NQE - 1 - q]);
             numflux(ph, g, sqg, wp[q], wm, hbq[q], nx, ny, Fh[q]);
           }
         }
@@ -713,12 +777,12 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
     }
 #pragma unroll
     for (int q = 0; q < NQE; ++q) {
-      const T wgt = weighted ? T(1) : hl * tb.we[q];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        const T f = wgt * Fh[q][v];
+        const T f = weighted ? Fh[q][v] : (hl * tb.we[q]) * Fh[q][v];
+        r[v][0] -= f;  // psi_00 = 1
 #pragma unroll
-        for (int k = 0; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
+        for (int k = 1; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
       }
     }
   }
@@ -785,12 +849,7 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
 #pragma unroll
   for (int q = 0; q < NQE; ++q) {
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      T acc = 0;
-#pragma unroll
-      for (int k = 0; k < ND; ++k) acc += wa[v][k] * s_phe[la][q][k];
-      ta[q][v] = acc;
-    }
+    for (int v = 0; v < 3; ++v) ta[q][v] = modal_value<ND, T>(wa[v], s_phe[la][q]);
     hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hA + (T(1) + tb.se[q]) * hB);
   }
   // slot of (element li, local edge l, Gauss point q, variable v)
@@ -805,12 +864,7 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
     for (int q = 0; q < NQE; ++q) {
       T tbq[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        T acc = 0;
-#pragma unroll
-        for (int k = 0; k < ND; ++k) acc += wb[v][k] * s_phe[lb][NQE - 1 - q][k];
-        tbq[v] = acc;
-      }
+      for (int v = 0; v < 3; ++v) tbq[v] = modal_value<ND, T>(wb[v], s_phe[lb][NQE - 1 - q]);
       const T wgt = hl * tb.we[q];
       if (flows) {
         T f[3];
@@ -898,8 +952,9 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
           const T f = s_slot[(size_t)((l * NQE + q) * 3 + v) * B + i];
+          r[v][0] -= f;  // psi_00 = 1
 #pragma unroll
-          for (int k = 0; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
+          for (int k = 1; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
         }
     elem_finish<P, T>(m, s, ph, write_rhs, e, c, r);
   }
