@@ -189,6 +189,7 @@ struct Tab {
   T inrm[MAXD];            // their inverses
   T phm[3][3];             // linear modes at the three edge midpoints
   T phv[3][MAXD];          // basis at the three vertices
+  T lim_idet;              // 1 / (phm[0][1] phm[1][2] - phm[0][2] phm[1][1]): linear modes from midpoints 0, 1
 };
 
 void build_tables(int p, Tab<double> &t);

@@ -136,6 +136,14 @@ template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt_d(x); }
+// a / b: through the seeded reciprocal only where b lies in its range; elsewhere the IEEE divide
+// (1/b overflows for subnormal b where a/b with |a| <= |b| stays finite)
+template <typename T>
+__device__ __forceinline__ T ratio_t(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ double ratio_t<double>(double a, double b) {
+  return seed_range(__double2hiint(b)) ? a * rcp_d(b) : a / b;
+}
 // x > 0 from the bits (an integer compare; positive NaN counts as positive and stays non-finite)
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool positive(float x) { return __float_as_int(x) > 0; }
@@ -654,11 +662,14 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
   const double dt = s.clk.dt;
   const size_t base = (size_t)ne;
   bool bad = false;
+  T minv[ND];  // inverse mass matrix diagonal: 1 / (|J| ||phi_k||^2)
+#pragma unroll
+  for (int k = 0; k < ND; ++k) minv[k] = idJ * tb.inrm[k];
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
 #pragma unroll
     for (int k = 0; k < ND; ++k) {
-      T L = r[v][k] * idJ * tb.inrm[k];
+      T L = r[v][k] * minv[k];
       if (k < 3) L += (v == 1) ? src1[k] : (v == 2 ? src2[k] : T(0));
       if (v == 0 && k == 0) L += (T)ph.rain;  // (phi_0, R) / (|J| ||phi_0||^2) = R
       const size_t ix = (size_t)(v * ND + k) * base + e;
@@ -976,10 +987,19 @@ __device__ __forceinline__ float minmod(float a, float b) {
   if (a < 0.f && b < 0.f) return a > b ? a : b;
   return 0.f;
 }
+// Double minmod from the bits (integer pipe): opposite signs (or a zero) give 0; otherwise the
+// operand of smaller magnitude (b on a tie), as the comparisons of the float version select.
 __device__ __forceinline__ double minmod(double a, double b) {
-  if (a > 0.0 && b > 0.0) return a < b ? a : b;
-  if (a < 0.0 && b < 0.0) return a > b ? a : b;
-  return 0.0;
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const unsigned long long ma = (unsigned long long)ia << 1, mb = (unsigned long long)ib << 1;  // |a|, |b|
+  if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0.0;
+  return ma < mb ? a : b;
+}
+// a != b as numbers for finite values (+0 equals -0), from the bits
+__device__ __forceinline__ bool differs(float a, float b) { return a != b; }
+__device__ __forceinline__ bool differs(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return ia != ib && ((ia | ib) << 1) != 0;
 }
 
 constexpr double WD_TOL = 1e-10;  // m: depths within this of h0 count as "at h0"
@@ -1005,19 +1025,18 @@ __device__ __noinline__ void limiter_rebuild(const T d[3], double *u1, double *u
   T tp = T(0), tm = T(0);
   if (pos > T(0) && neg > T(0)) {
     if (neg <= pos) {
-      tp = neg / pos;
+      tp = ratio_t(neg, pos);
       tm = T(1);
     } else {
       tp = T(1);
-      tm = pos / neg;
+      tm = ratio_t(pos, neg);
     }
   }
   T dh[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) dh[i] = tp * (d[i] > T(0) ? d[i] : T(0)) - tm * (d[i] < T(0) ? -d[i] : T(0));
-  const T det = tb.phm[0][1] * tb.phm[1][2] - tb.phm[0][2] * tb.phm[1][1];
-  *u1 = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) / det);
-  *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) / det);
+  *u1 = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) * tb.lim_idet);
+  *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) * tb.lim_idet);
 }
 
 template <int P, typename T>
@@ -1087,7 +1106,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
         T db = T(0);
         if (j1 != 3) db = A[(size_t)(2 * i) * ne + e] * (ub[j1] - u0) + A[(size_t)(2 * i + 1) * ne + e] * (ub[j2] - u0);
         d[i] = minmod(ut, nu * db);
-        act |= d[i] != ut;
+        act |= differs(d[i], ut);
       }
       if (!act) continue;
       any = true;
@@ -1113,7 +1132,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
       const float mag = fabsf(fz0) + fabsf(fz1) + 2.f * fabsf(fz2) + fmaxf(fabsf(fh0), fmaxf(fabsf(fh1), fabsf(fh2)));
       const float margin = 1e-6f * mag + 1e-6f;
       const float lo = fminf(fz0 - fz1 - fz2 + fh0, fminf(fz0 + fz1 - fz2 + fh1, fz0 + 2.f * fz2 + fh2));
-      if (lo > (float)h0 + margin) {
+      if (lo > d2f(h0) + margin) {
         if (do_wd == 1 || do_wd == 2) wd[e] = 0;
         return;
       }

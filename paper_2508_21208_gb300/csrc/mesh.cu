@@ -477,6 +477,7 @@ void build_tables(int p, Tab<double> &t) {
     for (int k = 0; k < 3; ++k) t.phm[l][k] = v[k];
     dubiner(V[l][0], V[l][1], t.phv[l], dx, dy);
   }
+  t.lim_idet = 1.0 / (t.phm[0][1] * t.phm[1][2] - t.phm[0][2] * t.phm[1][1]);
   const double nrm[MAXD] = {2.0, 1.0 / 3.0, 1.0, 2.0 / 15.0, 2.0 / 9.0, 2.0 / 3.0};
   for (int k = 0; k < MAXD; ++k) {
     t.nrm[k] = nrm[k];
