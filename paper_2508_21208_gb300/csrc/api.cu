@@ -91,6 +91,24 @@ Phys make_phys(const dgswem_params &p) {
   ph.flux = p.flux;
   ph.rain = p.rain_rate;
   ph.river_q = p.river_q;
+  PhysF &f = ph.f;
+  f.g = (float)ph.g;
+  f.sqrt_g = (float)ph.sqrt_g;
+  f.h0 = (float)ph.h0;
+  f.cf = (float)ph.cf;
+  f.gn2 = (float)ph.gn2;
+  f.fcor = (float)ph.fcor;
+  f.rain = (float)ph.rain;
+  f.river_q = (float)ph.river_q;
+  f.dp = (float)(ph.pn - ph.pc);
+  f.tx = 0.5f * (float)(ph.vt * ph.cos_h);
+  f.ty = 0.5f * (float)(ph.vt * ph.sin_h);
+  f.rmax = (float)ph.rmax;
+  f.hB = (float)ph.hB;
+  f.flat = (float)ph.flat;
+  f.hB_rho_air = (float)ph.hB_rho_air;
+  f.rho_ratio = (float)ph.rho_ratio;
+  f.inv_rho_w = (float)ph.inv_rho_w;
   return ph;
 }
 
@@ -254,6 +272,8 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
     sa.ra = c->ra[stage];
     sa.rb = c->rb[stage];
     sa.rc = c->rc[stage];
+    sa.rcdt = sa.rc * c->dt;
+    sa.rk_form = rk_form_of(sa.ra, sa.rb, sa.rc);
     sa.err = c->err;
     if (variant == DGSWEM_VARIANT_TILED) {
       mark(c, kname_element, names, &ev_i);
@@ -472,28 +492,47 @@ static int autotune(dgswem_ctx *c, int *best_variant, int *best_block) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // Per candidate: one replay to estimate the step time, then the best of three batches sized to
+  // about 1 ms each (short single samples cannot separate candidates a few percent apart).  The
+  // first candidate is also replayed for ~5 ms beforehand so that every trial sees warm clocks.
+  auto timed = [&](int n, float *ms) -> int {
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < n; ++i) cudaGraphLaunch(c->exec, s);
+    cudaEventRecord(e1, s);
+    if (int r = ctx_cuda(c, cudaEventSynchronize(e1), "tune timing")) return r;
+    cudaEventElapsedTime(ms, e0, e1);
+    return 0;
+  };
+  auto restore = [&]() {
+    cudaMemcpyAsync(c->U0, save_u.data(), nu * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->wd, save_wd.data(), c->hm.ne, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(c->step, 0, sizeof(long long), s);
+    cudaMemsetAsync(c->err, 0, sizeof(int), s);
+  };
   float best = INFINITY;
-  const int reps = c->hm.ne < 100000 ? 20 : 5;
+  bool warmed = false;
   for (int v : variants)
     for (int b : blocks) {
       if (int r = capture_graph(c, v, b, false)) return r;
-      cudaGraphLaunch(c->exec, s);
-      cudaEventRecord(e0, s);
-      for (int i = 0; i < reps; ++i) cudaGraphLaunch(c->exec, s);
-      cudaEventRecord(e1, s);
-      if (int r = ctx_cuda(c, cudaEventSynchronize(e1), "tune timing")) return r;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      c->tune_log.push_back({v, b, ms / reps});
-      if (ms < best) {
-        best = ms;
+      float t1 = 0, ms = 0;
+      if (int r = timed(1, &t1)) return r;
+      const int reps = std::min(200, std::max(3, (int)std::ceil(1.0f / std::max(t1, 1e-3f))));
+      if (!warmed) {
+        if (int r = timed(std::min(1000, 5 * reps), &ms)) return r;
+        warmed = true;
+      }
+      float per = INFINITY;
+      for (int k = 0; k < 3; ++k) {
+        if (int r = timed(reps, &ms)) return r;
+        per = std::min(per, ms / reps);
+      }
+      c->tune_log.push_back({v, b, per});
+      if (per < best) {
+        best = per;
         *best_variant = v;
         *best_block = b;
       }
-      cudaMemcpyAsync(c->U0, save_u.data(), nu * sizeof(double), cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(c->wd, save_wd.data(), c->hm.ne, cudaMemcpyHostToDevice, s);
-      cudaMemsetAsync(c->step, 0, sizeof(long long), s);
-      cudaMemsetAsync(c->err, 0, sizeof(int), s);
+      restore();
     }
   cudaStreamSynchronize(s);
   cudaEventDestroy(e0);
@@ -679,6 +718,8 @@ int dgswem_eval_rhs(dgswem_ctx *c, double t, double *h_out) {
   sa.ra = 0.0;
   sa.rb = 1.0;
   sa.rc = 1.0;
+  sa.rcdt = c->dt;
+  sa.rk_form = 0;
   sa.err = c->err;
   sa.tide_t = t;
   const bool split = c->variant == DGSWEM_VARIANT_SPLIT;

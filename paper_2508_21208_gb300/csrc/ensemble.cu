@@ -191,6 +191,7 @@ void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names) {
     a.rb[i] = c->rb[i];
     a.rc[i] = c->rc[i];
     a.tau[i] = c->rtau[i];
+    a.form[i] = rk_form_of(c->ra[i], c->rb[i], c->rc[i]);
   }
   a.mem = E.d_mem;
   a.etile = E.d_etile;
@@ -306,13 +307,18 @@ int ensemble_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream
       for (int b : blocks) {
         if (int r = configure(c, mode, b)) return r;
         cudaGraphLaunch(c->exec, c->st);
-        cudaEventRecord(e0, c->st);
+        // best of two batches of three steps (a step of a large ensemble is milliseconds long)
         const int reps = 3;
-        for (int i = 0; i < reps; ++i) cudaGraphLaunch(c->exec, c->st);
-        cudaEventRecord(e1, c->st);
-        if (int r = ctx_cuda(c, cudaEventSynchronize(e1), "ensemble tune")) return r;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
+        float ms = INFINITY;
+        for (int k = 0; k < 2; ++k) {
+          cudaEventRecord(e0, c->st);
+          for (int i = 0; i < reps; ++i) cudaGraphLaunch(c->exec, c->st);
+          cudaEventRecord(e1, c->st);
+          if (int r = ctx_cuda(c, cudaEventSynchronize(e1), "ensemble tune")) return r;
+          float t = 0;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms = std::min(ms, t);
+        }
         E.tune.push_back({mode ? 1 : 2, b, ms / reps});
         if (ms < best) {
           best = ms;

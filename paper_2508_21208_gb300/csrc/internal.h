@@ -74,6 +74,14 @@ int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, Hos
                     std::string &msg);
 
 // ------------------------------------------------------------------ device-side views
+// Float copies of the constants the float form uses, rounded once on the host (a double -> float
+// conversion in a kernel runs on GB300's FP64 pipe).
+struct PhysF {
+  float g, sqrt_g, h0, cf, gn2, fcor, rain, river_q;
+  float dp, tx, ty;  // pn - pc; half the translation velocity (x, y)
+  float rmax, hB, flat, hB_rho_air, rho_ratio, inv_rho_w;
+};
+
 struct Phys {
   double g, sqrt_g, h0, cf, gn2, fcor;
   double tide_amp, tide_omega, tide_phase;
@@ -82,7 +90,16 @@ struct Phys {
   double hB_rho_air, rho_ratio, inv_rho_w;  // B / rho_air, rho_air / rho_w, 1 / rho_w
   int friction, wetdry, limiter, hurricane, flux;
   double rain, river_q;
+  PhysF f;
 };
+
+// The stage update's form, chosen on the host from (a, b, c): 0 u_in + c dt L; 1 the exact average
+// (u^n + u_in + dt L) / 2; 2 the general a u^n + b u_in + c dt L.
+inline int rk_form_of(double a, double b, double c) {
+  if (a == 0.0 && b == 1.0) return 0;
+  if (a == 0.5 && b == 0.5 && c == 0.5) return 1;
+  return 2;
+}
 
 struct DevMesh {
   int ne, nn, nint;
@@ -128,6 +145,8 @@ struct StageArgs {
   Clock clk;
   double tau;              // stage time = clk.t0 + (step + tau) * clk.dt
   double ra, rb, rc;       // u_out = ra u^n + rb u_in + rc dt L(u_in)
+  double rcdt;             // rc * dt
+  int rk_form;             // rk_form_of(ra, rb, rc)
   int *err;
   double tide_t;           // stage time when clk.step is null (single operator calls)
 };
@@ -157,6 +176,7 @@ struct MemberDev {
 struct EnsArgs {
   int nstages;
   double ra[MAX_STAGES], rb[MAX_STAGES], rc[MAX_STAGES], tau[MAX_STAGES];
+  int form[MAX_STAGES];    // rk_form_of per stage
   const MemberDev *mem;
   const int *etile;        // element tile -> member
   const int *ntile;        // node tile -> member (members with a hurricane)

@@ -20,6 +20,14 @@ __device__ __forceinline__ const Tab<double> &ctab<double>(int p) { return c_td[
 template <>
 __device__ __forceinline__ const Tab<float> &ctab<float>(int p) { return c_tf[p - 1]; }
 
+// A physical constant in the arithmetic type: the double itself, or its host-rounded float copy.
+template <typename T>
+__device__ __forceinline__ T pc(double d, float f);
+template <>
+__device__ __forceinline__ double pc<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pc<float>(double, float f) { return f; }
+
 __device__ __forceinline__ double stage_time(const Clock &c, double tau, double fixed) {
   return c.step ? c.t0 + ((double)*c.step + tau) * c.dt : fixed;
 }
@@ -57,13 +65,17 @@ template <typename T>
 __device__ __forceinline__ double to_d(T x) { return (double)x; }
 template <>
 __device__ __forceinline__ double to_d<float>(float x) { return f2d(x); }
-// x / 2, exactly, by lowering the exponent field on the integer pipe (zero stays zero; numbers
-// too small for that fall back to a multiply).
+// x / 2 with IEEE round-to-nearest-even, on the integer pipe: lower the exponent field of a
+// normal result; below 2^-1021 (|x| = m 2^-1074 with an integer m) halve m and round half to even;
+// infinity and NaN pass through.
 __device__ __forceinline__ double half_exact(double x) {
-  const int hi = __double2hiint(x);
-  const int ex = (hi >> 20) & 0x7ff;
-  if (ex > 1 && ex < 0x7ff) return __hiloint2double(hi - 0x00100000, __double2loint(x));
-  return 0.5 * x;
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex > 1 && ex < 0x7ff) return __longlong_as_double(b - (1LL << 52));
+  if (ex == 0x7ff) return x;
+  const long long m = b & 0x7fffffffffffffffLL;
+  const long long h = (m >> 1) + ((m & 1) & ((m >> 1) & 1));
+  return __longlong_as_double((b & (long long)0x8000000000000000ULL) | h);
 }
 // finiteness from the exponent bits (no floating-point compare)
 __device__ __forceinline__ bool finite_bits(double x) {
@@ -264,7 +276,7 @@ __device__ __forceinline__ void numflux(const Phys &ph, T g, T sqrt_g, const T w
 
 template <typename T>
 __device__ __forceinline__ void river(const Phys &ph, T g, T sqrt_g, const T wi[3], T hb, T nx, T ny, T out[3]) {
-  const T d = T(2) * (wi[1] * nx + wi[2] * ny + (T)ph.river_q);
+  const T d = T(2) * (wi[1] * nx + wi[2] * ny + pc<T>(ph.river_q, ph.f.river_q));
   const T wo[3] = {wi[0], wi[1] - d * nx, wi[2] - d * ny};
   numflux(ph, g, sqrt_g, wi, wo, hb, nx, ny, out);
 }
@@ -280,8 +292,8 @@ __device__ __forceinline__ void wall(const Phys &ph, T g, T sqrt_g, const T wi[3
 template <typename T>
 __device__ __forceinline__ T friction_tau(const Phys &ph, T qx, T qy, T H, T iH) {
   const T qm = sqrt_t(qx * qx + qy * qy);
-  if (ph.friction == DGSWEM_FRICTION_QUADRATIC) return (T)ph.cf * qm * iH * iH;
-  if (ph.friction == DGSWEM_FRICTION_MANNING) return (T)ph.gn2 * qm * iH * iH * rcbrt(H);
+  if (ph.friction == DGSWEM_FRICTION_QUADRATIC) return pc<T>(ph.cf, ph.f.cf) * qm * iH * iH;
+  if (ph.friction == DGSWEM_FRICTION_MANNING) return pc<T>(ph.gn2, ph.f.gn2) * qm * iH * iH * rcbrt(H);
   return T(0);
 }
 
@@ -365,8 +377,8 @@ __device__ __forceinline__ void vortex_at(const Phys &ph, T dx, T dy, T &tx_out,
 // multiplications by host-computed constants.  Out of line, so that every kernel that evaluates it rounds identically.
 static __device__ __noinline__ void vortex_at_f(const Phys &ph, float dx, float dy, float *out) {
   const float r2 = dx * dx + dy * dy;
-  const float dp = (float)(ph.pn - ph.pc);
-  const float tx = 0.5f * (float)(ph.vt * ph.cos_h), ty = 0.5f * (float)(ph.vt * ph.sin_h);
+  const float dp = ph.f.dp;
+  const float tx = ph.f.tx, ty = ph.f.ty;
   float pa, ux, uy;
   if (r2 < 1.f) {
     pa = -dp;
@@ -374,20 +386,20 @@ static __device__ __noinline__ void vortex_at_f(const Phys &ph, float dx, float 
     uy = ty;
   } else {
     const float ir = rsqrtf(r2), r = r2 * ir;
-    const float A = exp2f((float)ph.hB * __log2f((float)ph.rmax * ir)), em1 = expm1f(-A), E = 1.f + em1;
+    const float A = exp2f(ph.f.hB * __log2f(ph.f.rmax * ir)), em1 = expm1f(-A), E = 1.f + em1;
     pa = dp * em1;
-    const float hf = 0.5f * r * (float)ph.flat;
-    const float V = sqrtf((float)ph.hB_rho_air * dp * A * E + hf * hf) - hf;
+    const float hf = 0.5f * r * ph.f.flat;
+    const float V = sqrtf(ph.f.hB_rho_air * dp * A * E + hf * hf) - hf;
     ux = 0.9f * V * (-dy * ir) + tx;
     uy = 0.9f * V * (dx * ir) + ty;
   }
   const float U = sqrtf(ux * ux + uy * uy);
   float cd = 0.75f + 0.067f * U;
   cd = (cd > 3.5f ? 3.5f : cd) * 1e-3f;
-  const float k = (float)ph.rho_ratio * cd * U;
+  const float k = ph.f.rho_ratio * cd * U;
   out[0] = k * ux;
   out[1] = k * uy;
-  out[2] = pa * (float)ph.inv_rho_w;
+  out[2] = pa * ph.f.inv_rho_w;
 }
 template <>
 __device__ __forceinline__ void vortex_at<float>(const Phys &ph, float dx, float dy, float &tx_out, float &ty_out,
@@ -455,7 +467,7 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
   T wp[3][ND], wm[3][ND];
   load_modes<P, T>(s.uin, ne, ep, wp);
   load_modes<P, T>(s.uin, ne, em, wm);
-  const T g = (T)ph.g, sqg = (T)ph.sqrt_g;
+  const T g = pc<T>(ph.g, ph.f.g), sqg = pc<T>(ph.sqrt_g, ph.f.sqrt_g);
   T *F = (T *)s.eflux;
 #pragma unroll
   for (int q = 0; q < NQE; ++q) {
@@ -517,7 +529,7 @@ template <int P, typename T>
 __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph, T r[3][nd_of(P)]) {
   constexpr int ND = nd_of(P), NQA = nqa_of(P);
   const Tab<T> &tb = ctab<T>(P);
-  const T g = (T)ph.g;
+  const T g = pc<T>(ph.g, ph.f.g);
   const T rx = c.rx, ry = c.ry, sx = c.sx, sy = c.sy, dJ = c.dJ;
   const T (&w)[3][ND] = c.w;
   const T (&hb)[3] = c.hb;
@@ -594,11 +606,11 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
 template <int P, typename T>
 __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s, const Phys &ph,
                                             const int write_rhs, const int e, const ElemCtx<P, T> &c,
-                                            T r[3][nd_of(P)]) {
+                                            T r[3][nd_of(P)], const double *ctr = nullptr) {
   constexpr int ND = nd_of(P);
   const Tab<T> &tb = ctab<T>(P);
   const int ne = m.ne;
-  const T g = (T)ph.g;
+  const T g = pc<T>(ph.g, ph.f.g);
   const T rx = c.rx, ry = c.ry, sx = c.sx, sy = c.sy, dJ = c.dJ;
   const T (&w)[3][ND] = c.w;
   const T (&hb)[3] = c.hb;
@@ -607,7 +619,7 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
   {
     const T hbx = T(0.5) * (rx * (hb[1] - hb[0]) + sx * (hb[2] - hb[0]));
     const T hby = T(0.5) * (ry * (hb[1] - hb[0]) + sy * (hb[2] - hb[0]));
-    const T fc = (T)ph.fcor;
+    const T fc = pc<T>(ph.fcor, ph.f.fcor);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       src1[k] = g * hbx * w[0][k] + fc * w[2][k];
@@ -618,9 +630,15 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
       const int n0 = m.vnode[e], n1 = m.vnode[ne + e], n2 = m.vnode[2 * (size_t)ne + e];
       T t0, t1, t2, u0, u1, u2, p0, p1, p2;
       if (s.frc_inline) {
-        // the centre once per element; vertex offsets in T (O(1e5) m coordinates, float ulp ~1 cm)
+        // the centre once per element (or per block: ctr); vertex offsets in T (O(1e5) m
+        // coordinates, float ulp ~1 cm)
         double cxd, cyd;
-        storm_center(ph, stage_time(s.clk, s.tau, s.tide_t), cxd, cyd);
+        if (ctr) {
+          cxd = ctr[0];
+          cyd = ctr[1];
+        } else {
+          storm_center(ph, stage_time(s.clk, s.tau, s.tide_t), cxd, cyd);
+        }
         const T cx = from_d<T>(cxd), cy = from_d<T>(cyd);
         vortex_at<T>(ph, from_d<T>(m.nodexy[n0]) - cx, from_d<T>(m.nodexy[nn + n0]) - cy, t0, u0, p0);
         vortex_at<T>(ph, from_d<T>(m.nodexy[n1]) - cx, from_d<T>(m.nodexy[nn + n1]) - cy, t1, u1, p1);
@@ -671,19 +689,19 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
     for (int k = 0; k < ND; ++k) {
       T L = r[v][k] * minv[k];
       if (k < 3) L += (v == 1) ? src1[k] : (v == 2 ? src2[k] : T(0));
-      if (v == 0 && k == 0) L += (T)ph.rain;  // (phi_0, R) / (|J| ||phi_0||^2) = R
+      if (v == 0 && k == 0) L += pc<T>(ph.rain, ph.f.rain);  // (phi_0, R) / (|J| ||phi_0||^2) = R
       const size_t ix = (size_t)(v * ND + k) * base + e;
       const double Ld = to_d<T>(L);
       double out;
       if (write_rhs) {
         out = Ld;
-      } else if (s.ra == 0.0 && s.rb == 1.0) {  // forward-Euler stage
-        out = s.uin[ix] + (s.rc * dt) * Ld;
-      } else if (s.ra == 0.5 && s.rb == 0.5 && s.rc == 0.5) {
+      } else if (s.rk_form == 0) {  // forward-Euler stage
+        out = fma(s.rcdt, Ld, s.uin[ix]);
+      } else if (s.rk_form == 1) {
         // u/2 + (u1 + dt L)/2 == (u + (u1 + dt L)) / 2 exactly (halving commutes with rounding)
         out = half_exact(s.un[ix] + (s.uin[ix] + dt * Ld));
       } else {
-        out = fma(s.rc * dt, Ld, s.ra * s.un[ix] + s.rb * s.uin[ix]);
+        out = fma(s.rcdt, Ld, s.ra * s.un[ix] + s.rb * s.uin[ix]);
       }
       bad |= !finite_bits(out);
       s.uout[ix] = out;
@@ -700,7 +718,7 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
   constexpr int ND = nd_of(P), NQE = nqe_of(P);
   const Tab<T> &tb = ctab<T>(P);
   const int ne = m.ne;
-  const T g = (T)ph.g, sqg = (T)ph.sqrt_g;
+  const T g = pc<T>(ph.g, ph.f.g), sqg = pc<T>(ph.sqrt_g, ph.f.sqrt_g);
   ElemCtx<P, T> c;
   elem_load<P, T>(m, s.uin, e, c);
   const T *geo = (const T *)m.geo;
@@ -845,7 +863,7 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
   constexpr int ND = nd_of(P), NQE = nqe_of(P);
   const Tab<T> &tb = ctab<T>(P);
   const int B = tl.tile, ne = m.ne;
-  const T g = (T)ph.g, sqg = (T)ph.sqrt_g;
+  const T g = pc<T>(ph.g, ph.f.g), sqg = pc<T>(ph.sqrt_g, ph.f.sqrt_g);
   const int a = tl.ea[x], b = tl.eb[x];
   const unsigned code = tl.code[x];
   const int la = code & 3u, lb = (code >> 2) & 3u;
@@ -937,6 +955,8 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
   uint8_t *s_wd = reinterpret_cast<uint8_t *>(s_slot + (size_t)9 * NQE * B);
   const int e0 = tile * B, i = threadIdx.x;
   const int nloc = min(B, ne - e0);
+  __shared__ double s_ctr[2];  // storm centre at the stage time, once per block (inline vortex)
+  if (s.frc_inline && i == 0) storm_center(ph, stage_time(s.clk, s.tau, s.tide_t), s_ctr[0], s_ctr[1]);
   if (i < nloc) {
 #pragma unroll
     for (int r = 0; r < 3 * ND; ++r) s_ud[r * B + i] = from_d<T>(__ldg(&s.uin[(size_t)r * ne + e0 + i]));
@@ -967,7 +987,7 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
 #pragma unroll
           for (int k = 1; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
         }
-    elem_finish<P, T>(m, s, ph, write_rhs, e, c, r);
+    elem_finish<P, T>(m, s, ph, write_rhs, e, c, r, s_ctr);
   }
   __syncthreads();  // the shared-memory tile is reused by the block's next tile
 }
@@ -1132,7 +1152,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
       const float mag = fabsf(fz0) + fabsf(fz1) + 2.f * fabsf(fz2) + fmaxf(fabsf(fh0), fmaxf(fabsf(fh1), fabsf(fh2)));
       const float margin = 1e-6f * mag + 1e-6f;
       const float lo = fminf(fz0 - fz1 - fz2 + fh0, fminf(fz0 + fz1 - fz2 + fh1, fz0 + 2.f * fz2 + fh2));
-      if (lo > d2f(h0) + margin) {
+      if (lo > ph.f.h0 + margin) {
         if (do_wd == 1 || do_wd == 2) wd[e] = 0;
         return;
       }
@@ -1271,6 +1291,8 @@ __device__ __forceinline__ StageArgs member_stage(const MemberDev &md, const Ens
   sa.ra = a.ra[stage];
   sa.rb = a.rb[stage];
   sa.rc = a.rc[stage];
+  sa.rcdt = sa.rc * md.dt;
+  sa.rk_form = a.form[stage];
   sa.err = a.err;
   sa.tide_t = 0.0;
   return sa;
