@@ -993,7 +993,7 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
 }
 
 template <int P, typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (P == 1 ? 4 : 2) : 1)
     k_tile(const DevMesh m, const DevTiles tl, const StageArgs s, const Phys ph, const int write_rhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
@@ -1348,7 +1348,7 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
 // held to 3 (p = 1) or 2 (p = 2) resident 256-thread blocks per SM: left free, the union of the
 // phases takes more registers than any phase needs and only 2 blocks fit.
 template <int P, typename T>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 3 : 2) : 1)) k_ens_persistent(const EnsArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 4 : 2) : 1)) k_ens_persistent(const EnsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   __shared__ MemberDev sd;
@@ -1373,7 +1373,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 3 : 2) : 1)) 
 
 // The same phases as separate launches (one tile per block); the stream orders them.
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_ens_phase(const EnsArgs a, int phase, int stage) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 4 : 2) : 1)) k_ens_phase(const EnsArgs a, int phase, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   __shared__ MemberDev sd;
