@@ -111,7 +111,7 @@ def recorded_traffic(kernel: str, form: str, elements: int, variant: int):
     for line in open(p):
         kv = dict(re.findall(r"(\w+)=(\S+)", line))
         if (kv.get("kernel") == kernel and kv.get("form") == form and kv.get("src_sha") == sha
-                and int(kv.get("variant", -1)) == variant):
+                and kv.get("variant") in ("*", str(variant))):
             # captured on a larger mesh (DRAM-resident); traffic per launch scales with elements
             return float(kv["bytes"]) / float(kv["elements"]) * elements
     return None
