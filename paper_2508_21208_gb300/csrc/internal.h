@@ -198,6 +198,7 @@ constexpr int ERR_TIMEOUT = 4;
 template <typename T>
 struct Tab {
   T wq[MAXQA];             // area weights on the reference triangle (area 2)
+  T iwq[MAXQA];            // their inverses
   T phq[MAXQA][MAXD];      // basis at area points
   T dxq[MAXQA][MAXD];      // d basis / d xi
   T dyq[MAXQA][MAXD];      // d basis / d eta

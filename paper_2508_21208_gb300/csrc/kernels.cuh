@@ -77,6 +77,7 @@ __device__ __forceinline__ double half_exact(double x) {
   const long long h = (m >> 1) + ((m & 1) & ((m >> 1) & 1));
   return __longlong_as_double((b & (long long)0x8000000000000000ULL) | h);
 }
+__device__ __forceinline__ double halve(double x) { return half_exact(x); }
 // finiteness from the exponent bits (no floating-point compare)
 __device__ __forceinline__ bool finite_bits(double x) {
   return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
@@ -172,44 +173,52 @@ __device__ __forceinline__ T modal_value(const T (&w)[ND], const T *ph) {
 
 // ------------------------------------------------------------------------ point physics
 // Normal flux F(w).n of Eq. SWE with the pressure term (g/2)(H^2 - h_b^2) = (g/2) zeta (zeta + 2 h_b).
+// One side of an edge point: q.n, u.n = q.n / H, the wave speed |u.n| + sqrt(g H) and the pressure
+// term P = (g/2) zeta (zeta + 2 h_b), so that F(w).n = (q.n, q_x u.n + P n_x, q_y u.n + P n_y).
+// 1/H and sqrt(g H) come from one reciprocal square root; H <= 0 falls back to a plain divide.
 template <typename T>
 struct Side {
-  T F[3];  // F(w).n
-  T s;     // |u.n| + sqrt(g H)
+  T qn, un, s, P;
 };
-
-// 1/H and sqrt(g H) come from one reciprocal square root; H <= 0 falls back to a plain divide.
 template <typename T>
 __device__ __forceinline__ Side<T> side_flux(T g, T sqrt_g, const T w[3], T hb, T nx, T ny) {
   Side<T> r;
   const T H = w[0] + hb;
-  const T qn = w[1] * nx + w[2] * ny;
-  T iH, c;
+  r.qn = w[1] * nx + w[2] * ny;
+  T c;
   if (positive(H)) {
     const T rs = rsqrt_t(H);
-    iH = rs * rs;
+    r.un = r.qn * rs * rs;
     c = sqrt_g * H * rs;
   } else {
-    iH = T(1) / H;
+    r.un = r.qn / H;
     c = T(0);
   }
-  const T un = qn * iH;
-  const T P = T(0.5) * g * w[0] * (w[0] + T(2) * hb);
-  r.F[0] = qn;
-  r.F[1] = w[1] * un + P * nx;
-  r.F[2] = w[2] * un + P * ny;
-  r.s = fabs(un) + c;
+  r.P = T(0.5) * g * w[0] * (w[0] + T(2) * hb);
+  r.s = fabs(r.un) + c;
   return r;
 }
 
-// Local Lax-Friedrichs flux (the numerical flux of Eq. elem_weak_form), n from wi to wo.
+// max of two non-negative numbers (ordered like their bit patterns: an integer compare)
+__device__ __forceinline__ float max_nonneg(float a, float b) { return __float_as_int(a) > __float_as_int(b) ? a : b; }
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
+}
+// x / 2: exact, on the integer pipe for double
+__device__ __forceinline__ float halve(float x) { return 0.5f * x; }
+
+// Local Lax-Friedrichs flux (the numerical flux of Eq. elem_weak_form), n from wi to wo:
+// (F(wi).n + F(wo).n)/2 - lam (wo - wi)/2 with lam the larger wave speed; the two pressure terms
+// are summed before the normal is applied.
 template <typename T>
 __device__ __forceinline__ void llf(T g, T sqrt_g, const T wi[3], const T wo[3], T hb, T nx, T ny, T out[3]) {
   const Side<T> a = side_flux(g, sqrt_g, wi, hb, nx, ny);
   const Side<T> b = side_flux(g, sqrt_g, wo, hb, nx, ny);
-  const T lam = a.s > b.s ? a.s : b.s;
-#pragma unroll
-  for (int v = 0; v < 3; ++v) out[v] = T(0.5) * (a.F[v] + b.F[v]) - T(0.5) * lam * (wo[v] - wi[v]);
+  const T lam = max_nonneg(a.s, b.s);
+  const T Ps = a.P + b.P;
+  out[0] = halve(a.qn + b.qn - lam * (wo[0] - wi[0]));
+  out[1] = halve(fma(wi[1], a.un, wo[1] * b.un) + Ps * nx - lam * (wo[1] - wi[1]));
+  out[2] = halve(fma(wi[2], a.un, wo[2] * b.un) + Ps * ny - lam * (wo[2] - wi[2]));
 }
 
 // Roe (1981) flux, n from wi to wo.  Edge frame (n, t = (-ny, nx)), state (H, q_n, q_t); Roe
@@ -287,14 +296,6 @@ __device__ __forceinline__ void wall(const Phys &ph, T g, T sqrt_g, const T wi[3
   const T qn = wi[1] * nx + wi[2] * ny;
   const T wo[3] = {wi[0], wi[1] - T(2) * qn * nx, wi[2] - T(2) * qn * ny};
   numflux(ph, g, sqrt_g, wi, wo, hb, nx, ny, out);
-}
-
-template <typename T>
-__device__ __forceinline__ T friction_tau(const Phys &ph, T qx, T qy, T H, T iH) {
-  const T qm = sqrt_t(qx * qx + qy * qy);
-  if (ph.friction == DGSWEM_FRICTION_QUADRATIC) return pc<T>(ph.cf, ph.f.cf) * qm * iH * iH;
-  if (ph.friction == DGSWEM_FRICTION_MANNING) return pc<T>(ph.gn2, ph.f.gn2) * qm * iH * iH * rcbrt(H);
-  return T(0);
 }
 
 // Wetting/drying edge rule: an edge touching a dry element carries no flow (each side sees a
@@ -541,7 +542,11 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
     T fr[2][ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) fr[0][k] = fr[1][k] = T(0);
-    T Gx = 0, Gy = 0, Hy = 0;  // P = 1: sums of w_q F at the points (grad phi is constant)
+    // The weight w_q is folded into the velocities, U = w_q q_x / H and V = w_q q_y / H, and the
+    // pressure term (g/2) zeta (zeta + 2 h_b) is summed without its factor g/2.  P = 1 (grad phi
+    // constant): Gx, Gy, Hy = sums of q_x U, q_x V, q_y V; Ps = sum of w_q zeta (zeta + 2 h_b).
+    T Gx = 0, Gy = 0, Hy = 0, Ps = 0;
+    const T hg = T(0.5) * g;
 #pragma unroll
     for (int q = 0; q < NQA; ++q) {
       const T z = modal_value<ND, T>(w[0], tb.phq[q]);
@@ -549,28 +554,36 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
       const T qy = modal_value<ND, T>(w[2], tb.phq[q]);
       const T hq = hb[0] * tb.nq[q][0] + hb[1] * tb.nq[q][1] + hb[2] * tb.nq[q][2];
       const T H = z + hq;
-      const T iH = rcp_t(H);
-      const T Pp = T(0.5) * g * z * (z + T(2) * hq);
-      const T u = qx * iH, v = qy * iH;
-      const T Fxx = qx * u + Pp, Fxy = qx * v, Fyy = qy * v + Pp;
       const T wq = tb.wq[q];
+      const T iHw = wq * rcp_t(H);
+      const T U = qx * iHw, V = qy * iHw;
+      const T Pw = wq * (z * (z + T(2) * hq));
       if constexpr (P == 1) {
-        Gx += wq * Fxx;
-        Gy += wq * Fxy;
-        Hy += wq * Fyy;
+        Gx += qx * U;
+        Gy += qx * V;
+        Hy += qy * V;
+        Ps += Pw;
       } else {
+        const T Pg = hg * Pw;
+        const T Fxx = qx * U + Pg, Fxy = qx * V, Fyy = qy * V + Pg;  // w_q F
 #pragma unroll
         for (int k = 1; k < ND; ++k) {
           const T gx = rx * tb.dxq[q][k] + sx * tb.dyq[q][k];
           const T gy = ry * tb.dxq[q][k] + sy * tb.dyq[q][k];
           r[0][k] += wq * (gx * qx + gy * qy);
-          r[1][k] += wq * (gx * Fxx + gy * Fxy);
-          r[2][k] += wq * (gx * Fxy + gy * Fyy);
+          r[1][k] += gx * Fxx + gy * Fxy;
+          r[2][k] += gx * Fxy + gy * Fyy;
         }
       }
       if (ph.friction) {
-        const T tw = wq * friction_tau<T>(ph, qx, qy, H, iH);
-        const T tx = tw * qx, ty = tw * qy;
+        // w_q tau_b q = c |q| q / H^2 w_q (times H^-1/3 for Manning) = c |U| U / w_q for H > 0;
+        // the sign of 1/w_q follows H so that the same holds for H < 0
+        T cq = pc<T>(ph.cf, ph.f.cf);
+        if (ph.friction == DGSWEM_FRICTION_MANNING) cq = pc<T>(ph.gn2, ph.f.gn2) * rcbrt(H);
+        else if (ph.friction != DGSWEM_FRICTION_QUADRATIC) cq = T(0);
+        const T Um = sqrt_t(U * U + V * V);
+        const T kq = cq * Um * (positive(H) ? tb.iwq[q] : -tb.iwq[q]);
+        const T tx = kq * U, ty = kq * V;
         fr[0][0] += tx;  // psi_00 = 1
         fr[1][0] += ty;
 #pragma unroll
@@ -579,6 +592,11 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
           fr[1][k] += ty * tb.phq[q][k];
         }
       }
+    }
+    if constexpr (P == 1) {
+      const T Pg = hg * Ps;
+      Gx += Pg;
+      Hy += Pg;
     }
     if constexpr (P == 1) {
       // grad psi_10 = J^-T (1, 1/2), grad psi_01 = J^-T (0, 3/2); the mass flux q is linear, so

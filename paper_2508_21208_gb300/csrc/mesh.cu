@@ -446,6 +446,7 @@ void build_tables(int p, Tab<double> &t) {
     double xi = l0 * V[0][0] + l1 * V[1][0] + l2 * V[2][0];
     double eta = l0 * V[0][1] + l1 * V[1][1] + l2 * V[2][1];
     t.wq[q] = 2.0 * pts[q][2];
+    t.iwq[q] = 1.0 / t.wq[q];
     dubiner(xi, eta, t.phq[q], t.dxq[q], t.dyq[q]);
     t.nq[q][0] = -0.5 * (xi + eta);
     t.nq[q][1] = 0.5 * (1.0 + xi);
