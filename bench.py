@@ -202,8 +202,18 @@ def cpu_baseline(case, budget_s=12.0):
         o.step(1)
         n += 1
     el = time.perf_counter() - t0
-    return {"value": case.mesh.n_elems * 2 * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} SSP-RK2 steps of the full 199,712-element shelf workload ({el:.1f} s, OpenMP build)"}
+    out = {"value": case.mesh.n_elems * 2 * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{n} SSP-RK2 steps of the full 199,712-element shelf workload ({el:.1f} s, OpenMP build)"}
+    # the plain single-thread build of the same source, on a shorter sample
+    o1 = oracle.Oracle(case.mesh, case.bathy, case.params, init_nodal=case.init_nodal, omp=False)
+    n1, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < budget_s / 3 and n1 < 100:
+        o1.step(1)
+        n1 += 1
+    el1 = time.perf_counter() - t1
+    out["single_thread"] = {"value": case.mesh.n_elems * 2 * n1 / el1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} steps of the same workload ({el1:.1f} s, serial build)"}
+    return out
 
 
 def e2e(case, steps, stream):

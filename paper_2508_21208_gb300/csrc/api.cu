@@ -89,6 +89,7 @@ Phys make_phys(const dgswem_params &p) {
   ph.limiter = p.limiter ? 1 : 0;
   ph.hurricane = p.hurricane ? 1 : 0;
   ph.flux = p.flux;
+  ph.holland15 = p.holland_b == 1.5 ? 1 : 0;
   ph.rain = p.rain_rate;
   ph.river_q = p.river_q;
   PhysF &f = ph.f;
@@ -138,7 +139,6 @@ static std::vector<char> typed(const std::vector<double> &v, bool mixed) {
 // ------------------------------------------------------------------ workspace layout
 void carve_mesh(Carver &k, const HostMesh &H, int p, bool mixed, DevMesh &m, int **perm, int **iperm) {
   const int ne = H.ne, nn = H.nn, nint = H.nint;
-  (void)p;
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
   m.ne = ne;
   m.nn = nn;
@@ -157,6 +157,9 @@ void carve_mesh(Carver &k, const HostMesh &H, int p, bool mixed, DevMesh &m, int
   m.edle = k.take<uint8_t>(nint);
   m.edgeo = k.take<char>(tsz * 3 * nint);
   m.edhb = k.take<double>(2 * (size_t)nint);
+  // h_b at quadrature points: read by the FP64 form only
+  m.hbq = mixed ? nullptr : k.take<char>(tsz * nqa_of(p) * ne);
+  m.edhbq = mixed ? nullptr : k.take<char>(tsz * nqe_of(p) * nint);
   m.nodexy = k.take<double>(2 * (size_t)nn);
   *perm = k.take<int>(ne);
   *iperm = k.take<int>(ne);
@@ -193,6 +196,7 @@ static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
   T.code = k.take<uint8_t>(mt);
   T.geo = k.take<char>(tsz * 3 * mt);
   T.hb = k.take<double>(2 * (size_t)mt);
+  T.hbq = c->mixed ? nullptr : k.take<char>(tsz * NQE * mt);
   *bytes = k.off;
 }
 
@@ -205,8 +209,14 @@ static int prepare_tiles(dgswem_ctx *c, int tile) {
   const int mt = max_tile_edges(c->hm);
   if (H.n > mt) return ctx_fail(c, DGSWEM_EINVAL, "tile edge list larger than its buffer");
   c->host_keep.push_back(typed(H.geo, c->mixed));
+  std::vector<double> hbq;
+  edge_point_hb(c->P, H.hb.data(), H.hb.data() + H.n, H.n, hbq);
+  c->host_keep.push_back(typed(hbq, c->mixed));
   cudaStream_t s = c->st;
   int r = 0;
+  if (T.hbq)
+    r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(T.hbq), c->host_keep.back().data(),
+                                     c->host_keep.back().size(), cudaMemcpyHostToDevice, s), "tiles");
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(T.start), H.start.data(), H.start.size() * sizeof(int),
                                    cudaMemcpyHostToDevice, s), "tiles");
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(T.ea), H.ea.data(), H.n * sizeof(int), cudaMemcpyHostToDevice, s),
@@ -215,8 +225,8 @@ static int prepare_tiles(dgswem_ctx *c, int tile) {
                 "tiles");
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<uint8_t *>(T.code), H.code.data(), H.n, cudaMemcpyHostToDevice, s),
                 "tiles");
-  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(T.geo), c->host_keep.back().data(), c->host_keep.back().size(),
-                                   cudaMemcpyHostToDevice, s), "tiles");
+  r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(T.geo), c->host_keep[c->host_keep.size() - 2].data(),
+                                   c->host_keep[c->host_keep.size() - 2].size(), cudaMemcpyHostToDevice, s), "tiles");
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<double *>(T.hb), H.hb.data(), H.hb.size() * sizeof(double),
                                    cudaMemcpyHostToDevice, s), "tiles");
   if (r) return c->sticky;
@@ -384,6 +394,13 @@ int upload_mesh(dgswem_ctx *c, const HostMesh &H, const DevMesh &m, int *perm, i
   c->host_keep.push_back(typed(H.geo, c->mixed));
   c->host_keep.push_back(typed(H.lima, c->mixed));
   c->host_keep.push_back(typed(H.edgeo, c->mixed));
+  {
+    std::vector<double> v;
+    area_point_hb(c->P, H, v);
+    c->host_keep.push_back(typed(v, c->mixed));
+    edge_point_hb(c->P, H.edhb.data(), H.edhb.data() + H.nint, H.nint, v);
+    c->host_keep.push_back(typed(v, c->mixed));
+  }
   int r = 0;
   r |= put(m.geo, c->host_keep[base].data(), c->host_keep[base].size());
   r |= put(m.hbv, H.hbv.data(), H.hbv.size() * sizeof(double));
@@ -399,6 +416,8 @@ int upload_mesh(dgswem_ctx *c, const HostMesh &H, const DevMesh &m, int *perm, i
   r |= put(m.edle, H.edle.data(), H.edle.size());
   r |= put(m.edgeo, c->host_keep[base + 2].data(), c->host_keep[base + 2].size());
   r |= put(m.edhb, H.edhb.data(), H.edhb.size() * sizeof(double));
+  if (m.hbq) r |= put(m.hbq, c->host_keep[base + 3].data(), c->host_keep[base + 3].size());
+  if (m.edhbq) r |= put(m.edhbq, c->host_keep[base + 4].data(), c->host_keep[base + 4].size());
   r |= put(m.nodexy, H.nodexy.data(), H.nodexy.size() * sizeof(double));
   r |= put(perm, H.perm.data(), H.perm.size() * sizeof(int));
   r |= put(iperm, H.iperm.data(), H.iperm.size() * sizeof(int));

@@ -67,6 +67,7 @@ static void ens_layout(dgswem_ctx *c, char *base, size_t *bytes) {
     m.dt.code = k.take<uint8_t>(mt);
     m.dt.geo = k.take<char>(tsz * 3 * mt);
     m.dt.hb = k.take<double>(2 * (size_t)mt);
+    m.dt.hbq = c->mixed ? nullptr : k.take<char>(tsz * nqe_of(c->P) * mt);
   }
   size_t stage = 0;
   for (EnsMember &mb : E.mem) {
@@ -219,11 +220,18 @@ static int upload_mesh_tiles(dgswem_ctx *c, EnsMesh &M, int tile) {
   if (M.dt.tile == tile) return 0;
   build_tile_edges(M.hm, tile, M.ht);
   if (M.ht.n > max_tile_edges(M.hm)) return ctx_fail(c, DGSWEM_EINVAL, "tile list larger than its buffer");
-  std::vector<char> geo(M.ht.geo.size() * (c->mixed ? 4 : 8));
-  for (size_t i = 0; i < M.ht.geo.size(); ++i) {
-    if (c->mixed) reinterpret_cast<float *>(geo.data())[i] = (float)M.ht.geo[i];
-    else reinterpret_cast<double *>(geo.data())[i] = M.ht.geo[i];
-  }
+  auto typed = [&](const std::vector<double> &v) {
+    std::vector<char> out(v.size() * (c->mixed ? 4 : 8));
+    for (size_t i = 0; i < v.size(); ++i) {
+      if (c->mixed) reinterpret_cast<float *>(out.data())[i] = (float)v[i];
+      else reinterpret_cast<double *>(out.data())[i] = v[i];
+    }
+    return out;
+  };
+  const std::vector<char> geo = typed(M.ht.geo);
+  std::vector<double> hbq_d;
+  edge_point_hb(c->P, M.ht.hb.data(), M.ht.hb.data() + M.ht.n, M.ht.n, hbq_d);
+  const std::vector<char> hbq = typed(hbq_d);
   cudaStream_t s = c->st;
   int r = 0;
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(M.dt.start), M.ht.start.data(), M.ht.start.size() * sizeof(int),
@@ -232,6 +240,9 @@ static int upload_mesh_tiles(dgswem_ctx *c, EnsMesh &M, int tile) {
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<int *>(M.dt.eb), M.ht.eb.data(), M.ht.n * sizeof(int), cudaMemcpyHostToDevice, s), "tiles");
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<uint8_t *>(M.dt.code), M.ht.code.data(), M.ht.n, cudaMemcpyHostToDevice, s), "tiles");
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(M.dt.geo), geo.data(), geo.size(), cudaMemcpyHostToDevice, s), "tiles");
+  if (M.dt.hbq)
+    r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<void *>(M.dt.hbq), hbq.data(), hbq.size(), cudaMemcpyHostToDevice, s),
+                  "tiles");
   r |= ctx_cuda(c, cudaMemcpyAsync(const_cast<double *>(M.dt.hb), M.ht.hb.data(), M.ht.hb.size() * sizeof(double),
                                    cudaMemcpyHostToDevice, s), "tiles");
   if (r) return c->sticky;

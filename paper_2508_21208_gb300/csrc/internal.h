@@ -89,6 +89,7 @@ struct Phys {
   double cos_h, sin_h;     // heading direction of the storm track
   double hB_rho_air, rho_ratio, inv_rho_w;  // B / rho_air, rho_air / rho_w, 1 / rho_w
   int friction, wetdry, limiter, hurricane, flux;
+  int holland15;           // B = 1.5: (Rmax/r)^B = s sqrt(s)
   double rain, river_q;
   PhysF f;
 };
@@ -117,6 +118,8 @@ struct DevMesh {
   const uint8_t *edle;     // [nint]
   const void *edgeo;       // T [3][nint]
   const double *edhb;      // [2][nint]
+  const void *hbq;         // T [NQA][ne]: h_b at the area quadrature points
+  const void *edhbq;       // T [NQE][nint]: h_b at the interior edges' Gauss points
   const double *nodexy;    // [2][nn]
 };
 
@@ -158,6 +161,7 @@ struct DevTiles {
   const uint8_t *code;     // [n]
   const void *geo;         // T [3][n]
   const double *hb;        // [2][n]
+  const void *hbq;         // T [NQE][n]: h_b at the Gauss points
   int n;
 };
 
@@ -214,6 +218,12 @@ struct Tab {
 };
 
 void build_tables(int p, Tab<double> &t);
+// h_b at the area quadrature points of every element ([NQA][ne]) and at the Gauss points of n
+// edges from their end values hA, hB ([NQE][n]), with the reference tables of degree p.  Computed
+// once on the host (in the FP64 form, an interpolation per point and stage costs more FP64 issue
+// than reading the value).
+void area_point_hb(int p, const HostMesh &H, std::vector<double> &out);
+void edge_point_hb(int p, const double *hA, const double *hB, int n, std::vector<double> &out);
 
 // launchers (kernels_f64.cu: T = double; kernels_f32.cu: T = float)
 struct LaunchCfg {

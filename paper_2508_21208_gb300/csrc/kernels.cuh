@@ -347,7 +347,7 @@ __device__ __forceinline__ void storm_center(const Phys &ph, double t, double &c
 // Forcing at a point (dx, dy) from the storm centre: tau/rho_w and (p - pn)/rho_w.
 template <typename T>
 __device__ __forceinline__ void vortex_at(const Phys &ph, T dx, T dy, T &tx_out, T &ty_out, T &pa_out) {
-  const T r = sqrt(dx * dx + dy * dy);
+  const T r = sqrt_t(dx * dx + dy * dy);
   const T dp = (T)(ph.pn - ph.pc);
   const T tx = T(0.5) * (T)(ph.vt * ph.cos_h), ty = T(0.5) * (T)(ph.vt * ph.sin_h);
   T pa, ux, uy;
@@ -356,21 +356,23 @@ __device__ __forceinline__ void vortex_at(const Phys &ph, T dx, T dy, T &tx_out,
     ux = tx;
     uy = ty;
   } else {
-    // anomaly (pn - pc) (exp(-A) - 1) from expm1: no cancellation where A is small (far field)
-    const T A = pow((T)ph.rmax / r, (T)ph.hB), em1 = expm1(-A), E = T(1) + em1;
+    // anomaly (pn - pc) (exp(-A) - 1) from expm1: no cancellation where A is small (far field);
+    // the usual Holland B = 1.5 takes (Rmax/r)^B = s sqrt(s) instead of a general power
+    const T ir = rcp_t(r), sr = (T)ph.rmax * ir;
+    const T A = ph.holland15 ? sr * sqrt_t(sr) : pow(sr, (T)ph.hB), em1 = expm1(-A), E = T(1) + em1;
     pa = dp * em1;
     const T hf = T(0.5) * r * (T)ph.flat;
-    const T V = sqrt((T)ph.hB_rho_air * dp * A * E + hf * hf) - hf;
-    ux = T(0.9) * V * (-dy / r) + tx;
-    uy = T(0.9) * V * (dx / r) + ty;
+    const T V = sqrt_t((T)ph.hB_rho_air * dp * A * E + hf * hf) - hf;
+    ux = T(0.9) * V * (-dy * ir) + tx;
+    uy = T(0.9) * V * (dx * ir) + ty;
   }
-  const T U = sqrt(ux * ux + uy * uy);
+  const T U = sqrt_t(ux * ux + uy * uy);
   T cd = T(0.75) + T(0.067) * U;
   cd = (cd > T(3.5) ? T(3.5) : cd) * T(1e-3);
   const T k = (T)ph.rho_ratio * cd * U;
   tx_out = k * ux;
   ty_out = k * uy;
-  pa_out = pa / (T)ph.rho_w;
+  pa_out = pa * (T)ph.inv_rho_w;
 }
 
 // The mixed form's vortex: one reciprocal square root for 1/r, the hardware log2/exp2
@@ -478,7 +480,11 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
       a[v] = modal_value<ND, T>(wp[v], s_phe[lp][q]);
       b[v] = modal_value<ND, T>(wm[v], s_phe[lm][NQE - 1 - q]);
     }
-    const T hb = T(0.5) * ((T(1) - tb.se[q]) * from_d<T>(hbA) + (T(1) + tb.se[q]) * from_d<T>(hbB));
+    T hb;  // h_b at the point (as in the area integrals: read in FP64, interpolated in float)
+    if constexpr (sizeof(T) == sizeof(double))
+      hb = ((const T *)m.edhbq)[(size_t)q * nint + d];
+    else
+      hb = T(0.5) * ((T(1) - tb.se[q]) * from_d<T>(hbA) + (T(1) + tb.se[q]) * from_d<T>(hbB));
     T f[3];
     numflux(ph, g, sqg, a, b, hb, nx, ny, f);
     const T wgt = hl * tb.we[q];
@@ -527,7 +533,8 @@ __device__ __forceinline__ void elem_load(const DevMesh &m, const double *u, int
 
 // Area integrals (Alg. 1): advective + pressure flux and friction, r_k set (not accumulated).
 template <int P, typename T>
-__device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph, T r[3][nd_of(P)]) {
+__device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph, T r[3][nd_of(P)],
+                                          const DevMesh &m, const int e) {
   constexpr int ND = nd_of(P), NQA = nqa_of(P);
   const Tab<T> &tb = ctab<T>(P);
   const T g = pc<T>(ph.g, ph.f.g);
@@ -552,7 +559,13 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
       const T z = modal_value<ND, T>(w[0], tb.phq[q]);
       const T qx = modal_value<ND, T>(w[1], tb.phq[q]);
       const T qy = modal_value<ND, T>(w[2], tb.phq[q]);
-      const T hq = hb[0] * tb.nq[q][0] + hb[1] * tb.nq[q][1] + hb[2] * tb.nq[q][2];
+      // h_b at the point: read in the FP64 form (host-computed; an FP64 interpolation costs more
+      // issue than the load), interpolated in the latency-bound float form
+      T hq;
+      if constexpr (sizeof(T) == sizeof(double))
+        hq = ((const T *)m.hbq)[(size_t)q * m.ne + e];
+      else
+        hq = hb[0] * tb.nq[q][0] + hb[1] * tb.nq[q][1] + hb[2] * tb.nq[q][2];
       const T H = z + hq;
       const T wq = tb.wq[q];
       const T iHw = wq * rcp_t(H);
@@ -744,7 +757,7 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
   const T (&hb)[3] = c.hb;
   const double (&hbd)[3] = c.hbd;
   T r[3][ND];
-  elem_area<P, T>(c, ph, r);
+  elem_area<P, T>(c, ph, r, m, e);
 
   // ---------------- edge integrals (Alg. 2 + Alg. 3), gathered per element in a fixed order
   const uint8_t fe = s.wd ? s.wd[e] : 0;
@@ -897,7 +910,10 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
   for (int q = 0; q < NQE; ++q) {
 #pragma unroll
     for (int v = 0; v < 3; ++v) ta[q][v] = modal_value<ND, T>(wa[v], s_phe[la][q]);
-    hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hA + (T(1) + tb.se[q]) * hB);
+    if constexpr (sizeof(T) == sizeof(double))  // h_b at the point (see the area integrals)
+      hbq[q] = ((const T *)tl.hbq)[(size_t)q * tl.n + x];
+    else
+      hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hA + (T(1) + tb.se[q]) * hB);
   }
   // slot of (element li, local edge l, Gauss point q, variable v)
   auto slot = [&](int li, int l, int q, int v) -> T & { return s_slot[(size_t)((l * NQE + q) * 3 + v) * B + li]; };
@@ -993,7 +1009,7 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
 #pragma unroll
       for (int k = 0; k < ND; ++k) c.w[v][k] = s_ud[(v * ND + k) * B + i];
     T r[3][ND];
-    elem_area<P, T>(c, ph, r);
+    elem_area<P, T>(c, ph, r, m, e);
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll

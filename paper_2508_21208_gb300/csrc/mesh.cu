@@ -404,6 +404,26 @@ int rk_stage_table(const dgswem_params &p, double a[MAX_STAGES], double b[MAX_ST
   return s;
 }
 
+void area_point_hb(int p, const HostMesh &H, std::vector<double> &out) {
+  Tab<double> t;
+  build_tables(p, t);
+  const int nqa = nqa_of(p), ne = H.ne;
+  out.assign((size_t)nqa * ne, 0.0);
+  for (int q = 0; q < nqa; ++q)
+    for (int e = 0; e < ne; ++e)
+      out[(size_t)q * ne + e] = H.hbv[e] * t.nq[q][0] + H.hbv[(size_t)ne + e] * t.nq[q][1] +
+                                H.hbv[2 * (size_t)ne + e] * t.nq[q][2];
+}
+
+void edge_point_hb(int p, const double *hA, const double *hB, int n, std::vector<double> &out) {
+  Tab<double> t;
+  build_tables(p, t);
+  const int nqe = nqe_of(p);
+  out.assign((size_t)nqe * n, 0.0);
+  for (int q = 0; q < nqe; ++q)
+    for (int x = 0; x < n; ++x) out[(size_t)q * n + x] = 0.5 * ((1.0 - t.se[q]) * hA[x] + (1.0 + t.se[q]) * hB[x]);
+}
+
 // ------------------------------------------------------------------ reference tables
 // Dubiner basis (Sec. 2.2, Eq. dubiner) psi_ij = P_i(a) ((1-b)/2)^i P_j^(2i+1,0)(b), written out
 // for i + j <= 2, with its reference gradient.

@@ -80,3 +80,20 @@ def test_withheld_barrier_arrival_times_out():
     ok = Ensemble(meshes, bathys, members, block=64, mode=ENSEMBLE_PERSISTENT)
     ok.step(2)
     ok.sync()
+
+
+def test_fp64_one_storm_per_standard_mesh_matches_oracle():
+    """One FP64 storm on each of the four ensemble meshes (49,928 / 199,712 / 399,618 / 798,848
+    elements), batched in one launch, against the oracle after 20 steps."""
+    meshes, bathys, members = synth.ensemble(members_per_mesh=1, precision=synth.FP64)
+    ens = Ensemble(meshes, bathys, members, mode=ENSEMBLE_PERSISTENT)
+    ens.step(20)
+    for i, (mi, prm, _) in enumerate(members):
+        o = oracle.Oracle(meshes[mi], bathys[mi], prm, omp=True)
+        assert ens.info(i)[0] == pytest.approx(o.dt, rel=1e-14)
+        o.step(20)
+        a, b = ens.state(i), o.state()
+        assert np.abs(b[1]).max() > 0.0  # the storm moved water
+        for v in range(3):
+            rel = np.linalg.norm(a[v] - b[v]) / max(np.linalg.norm(b[v]), 1e-300)
+            assert rel <= 1e-12, (i, v, rel)
