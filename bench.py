@@ -358,7 +358,7 @@ def main():
             "config": {"workload": "shelf-199712 (316x316 cells, tide, wet/dry, limiter, FP64, p=1)",
                        "global_batch": ne * world, "parallelism": f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps", "variant": variant,
-                       "block": block},
+                       "block": block, "autotune_ms_per_step": model.tune_log()},
             "gpu_launches": kps * args.steps,
             "hbm_gbs_algorithmic": ALG_BYTES[("fp64", 1)] * value / world / 1e9,
             "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,

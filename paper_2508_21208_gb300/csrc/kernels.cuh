@@ -1068,8 +1068,9 @@ constexpr double WD_TOL = 1e-10;  // m: depths within this of h0 count as "at h0
 // speculatively for every element: rescale the limited midpoint deviations so that they sum to
 // zero (theta+/- rule) and rebuild the linear modes from the midpoints of local edges 0 and 1.
 template <int P, typename T>
-__device__ __noinline__ void limiter_rebuild(const T d[3], double *u1, double *u2) {
+__device__ __noinline__ void limiter_rebuild(const T d0, const T d1, const T d2, double *u1, double *u2) {
   const Tab<T> &tb = ctab<T>(P);
+  const T d[3] = {d0, d1, d2};
   T pos = 0, neg = 0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -1089,8 +1090,14 @@ __device__ __noinline__ void limiter_rebuild(const T d[3], double *u1, double *u
   T dh[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) dh[i] = tp * (d[i] > T(0) ? d[i] : T(0)) - tm * (d[i] < T(0) ? -d[i] : T(0));
-  *u1 = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) * tb.lim_idet);
-  *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) * tb.lim_idet);
+  if constexpr (sizeof(T) == sizeof(double)) {
+    // inverse of the midpoint map above: dh0 = (u1 + u2)/2, dh1 = (u2 - u1)/2
+    *u1 = dh[0] - dh[1];
+    *u2 = dh[0] + dh[1];
+  } else {
+    *u1 = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) * tb.lim_idet);
+    *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) * tb.lim_idet);
+  }
 }
 
 template <int P, typename T>
@@ -1147,24 +1154,38 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
       const T u0 = from_d<T>(d0);
       const T u1 = from_d<T>(d1);
       const T u2 = from_d<T>(d2);
-      T ub[3];
+      T dd[3];  // neighbour mean minus own mean
 #pragma unroll
-      for (int j = 0; j < 3; ++j) ub[j] = from_d<T>(db3[j]);
+      for (int j = 0; j < 3; ++j) dd[j] = from_d<T>(db3[j]) - u0;
+      // midpoint deviations of the linear part; in double from the linear Dubiner modes at the
+      // edge midpoints, (1/2, 1/2), (-1/2, 1/2) and (0, -1) (Eq. dubiner): the same values as the
+      // table products (halving is exact), from two additions
+      T ut[3];
+      if constexpr (sizeof(T) == sizeof(double)) {
+        ut[0] = half_exact(u1 + u2);
+        ut[1] = half_exact(u2 - u1);
+        ut[2] = -u2;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) ut[i] = u1 * tb.phm[i][1] + u2 * tb.phm[i][2];
+      }
       T d[3];
       bool act = false;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const T ut = u1 * tb.phm[i][1] + u2 * tb.phm[i][2];
         const unsigned c = (code >> (4 * i)) & 15u;
         const int j1 = c & 3, j2 = c >> 2;
+        // select without dynamic register indexing (which would place dd in local memory)
+        const T x1 = j1 == 0 ? dd[0] : (j1 == 1 ? dd[1] : dd[2]);
+        const T x2 = j2 == 0 ? dd[0] : (j2 == 1 ? dd[1] : dd[2]);
         T db = T(0);
-        if (j1 != 3) db = A[(size_t)(2 * i) * ne + e] * (ub[j1] - u0) + A[(size_t)(2 * i + 1) * ne + e] * (ub[j2] - u0);
-        d[i] = minmod(ut, nu * db);
-        act |= differs(d[i], ut);
+        if (j1 != 3) db = A[(size_t)(2 * i) * ne + e] * x1 + A[(size_t)(2 * i + 1) * ne + e] * x2;
+        d[i] = minmod(ut[i], nu * db);
+        act |= differs(d[i], ut[i]);
       }
       if (!act) continue;
       any = true;
-      limiter_rebuild<P, T>(d, u + (size_t)(v * ND + 1) * ne + e, u + (size_t)(v * ND + 2) * ne + e);
+      limiter_rebuild<P, T>(d[0], d[1], d[2], u + (size_t)(v * ND + 1) * ne + e, u + (size_t)(v * ND + 2) * ne + e);
     }
     if constexpr (P == 2) {
       if (any)
