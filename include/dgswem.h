@@ -103,7 +103,7 @@ typedef struct {
   int32_t precision; /* DGSWEM_FP64 or DGSWEM_FP32_MIXED */
   double g;          /* gravity */
   double cfl;        /* dt = cfl * 3/(2p+1) * min_e r_e / lambda_e (r_e inradius) unless dt > 0 */
-  double dt;         /* > 0: fixed time step overriding cfl */
+  double dt;         /* > 0: fixed time step overriding cfl; 0: from cfl; < 0: DGSWEM_EINVAL */
   double h0;         /* wetting/drying minimum depth; 0 disables wetting/drying */
   int32_t friction;  /* DGSWEM_FRICTION_* */
   double manning_n, cf;

@@ -37,8 +37,16 @@ int check_params(const dgswem_params *p, std::string &msg) {
     msg = "params: unknown precision"; return DGSWEM_EINVAL;
   }
   if (!(p->g > 0) || !std::isfinite(p->g)) { msg = "params: g must be positive"; return DGSWEM_EINVAL; }
+  {
+    const double f[] = {p->g, p->cfl, p->dt, p->h0, p->manning_n, p->cf, p->coriolis_lat_deg, p->tide_amp,
+                        p->tide_period, p->tide_phase, p->pc_hpa, p->pn_hpa, p->rmax_m, p->holland_b, p->vt_ms,
+                        p->track_x0, p->track_y0, p->track_heading, p->rho_air, p->rho_water, p->rain_rate,
+                        p->river_q};
+    for (double x : f)
+      if (!std::isfinite(x)) { msg = "params: non-finite value"; return DGSWEM_EINVAL; }
+  }
+  if (p->dt < 0) { msg = "params: dt must be >= 0 (0: from cfl)"; return DGSWEM_EINVAL; }
   if (!(p->dt > 0) && !(p->cfl > 0)) { msg = "params: need dt > 0 or cfl > 0"; return DGSWEM_EINVAL; }
-  if (!std::isfinite(p->dt) || !std::isfinite(p->cfl)) { msg = "params: non-finite dt or cfl"; return DGSWEM_EINVAL; }
   if (p->h0 < 0 || !std::isfinite(p->h0)) { msg = "params: h0 must be >= 0"; return DGSWEM_EINVAL; }
   if (p->friction < 0 || p->friction > 2) { msg = "params: unknown friction law"; return DGSWEM_EINVAL; }
   if (p->friction == DGSWEM_FRICTION_QUADRATIC && !(p->cf >= 0)) { msg = "params: cf < 0"; return DGSWEM_EINVAL; }

@@ -88,3 +88,44 @@ def test_nan_bathymetry_rejected(lib):
     hb[3] = np.nan
     rc, h = _create(c.mesh, hb, c.params)
     assert rc == -1
+
+
+@pytest.mark.parametrize("key,val", [("flux", 2), ("rk_scheme", 9), ("rain_rate", float("nan")),
+                                     ("river_q", float("inf")), ("dt", -1.0), ("tide_phase", float("nan")),
+                                     ("cf", float("inf"))])
+def test_more_invalid_params_rejected(lib, key, val):
+    c = synth.config1(n=4)
+    prm = dict(c.params)
+    prm[key] = val
+    rc, h = _create(c.mesh, c.bathy, prm)
+    assert rc == -1 and not h
+
+
+def test_custom_rk_table_with_nan_rejected(lib):
+    c = synth.config1(n=4)
+    prm = dict(c.params, rk_scheme=synth.RK_CUSTOM, rk_stages=2, rk_coeffs=[0, 1, 1, 0.5, 0.5, float("nan")])
+    rc, h = _create(c.mesh, c.bathy, prm)
+    assert rc == -1 and not h
+
+
+def _one_triangle(p2):
+    xy = np.array([[0.0, 0.0], [1000.0, 0.0], p2])
+    return synth.Mesh(xy, np.array([[0, 1, 2]], np.int32), np.array([[0, 1], [1, 2], [2, 0]], np.int32),
+                      np.zeros(3, np.int32))
+
+
+def test_empty_mesh_rejected(lib):
+    m = synth.Mesh(np.zeros((0, 2)), np.zeros((0, 3), np.int32), np.zeros((0, 2), np.int32), np.zeros(0, np.int32))
+    rc, h = _create(m, np.zeros(0), synth.config1(n=4).params)
+    assert rc == -1 and not h
+
+
+def test_zero_area_triangle_rejected(lib):
+    rc, h = _create(_one_triangle([2000.0, 0.0]), np.full(3, 10.0), synth.config1(n=4).params)
+    assert rc == -2 and not h
+
+
+def test_single_triangle_accepted(lib):
+    rc, h = _create(_one_triangle([0.0, 1000.0]), np.full(3, 10.0), synth.config1(n=4).params)
+    assert rc == 0 and h
+    lib.dgswem_destroy(h)
