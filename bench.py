@@ -278,6 +278,7 @@ def main():
                     help="run 3 steps of one workload in a fixed launch configuration (for ncu)")
     ap.add_argument("--variant", type=int, default=1, help="with --profile: 1 split, 2 fused, 3 tiled")
     ap.add_argument("--block", type=int, default=64, help="with --profile: threads per block / tile size")
+    ap.add_argument("--profile-steps", type=int, default=3, help="with --profile: steps to run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -305,9 +306,9 @@ def main():
         mixed = synth.FP32_MIXED if args.profile.endswith("mixed") else synth.FP64
         case = synth.config3(precision=mixed) if args.profile.startswith("storm") else synth.config2(precision=mixed)
         m = make_model(case, torch.cuda.Stream(), variant=args.variant, block=args.block)
-        m.step(3)
+        m.step(args.profile_steps)
         m.sync()
-        print(json.dumps({"profile": args.profile, "elements": case.mesh.n_elems, "steps": 3,
+        print(json.dumps({"profile": args.profile, "elements": case.mesh.n_elems, "steps": args.profile_steps,
                           "variant": args.variant, "block": args.block}))
         return
     dist = None

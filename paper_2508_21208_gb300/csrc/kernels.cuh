@@ -1071,6 +1071,36 @@ template <int P, typename T>
 __device__ __noinline__ void limiter_rebuild(const T d0, const T d1, const T d2, double *u1, double *u2) {
   const Tab<T> &tb = ctab<T>(P);
   const T d[3] = {d0, d1, d2};
+  if constexpr (sizeof(T) == sizeof(double)) {
+    // the same arithmetic with the sign tests, the maxima with zero and the ordering of the two
+    // non-negative sums taken from the bits (integer pipe)
+    double dp[3], dn[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const bool nonneg = __double_as_longlong(d[i]) >= 0;  // sign bit clear
+      dp[i] = nonneg ? d[i] : 0.0;
+      dn[i] = nonneg ? 0.0 : -d[i];
+    }
+    const double pos = dp[0] + dp[1] + dp[2], neg = dn[0] + dn[1] + dn[2];
+    double tp = 0.0, tm = 0.0;
+    const long long bp = __double_as_longlong(pos), bn = __double_as_longlong(neg);
+    if (bp > 0 && bn > 0) {  // both positive
+      if (bn <= bp) {
+        tp = ratio_t(neg, pos);
+        tm = 1.0;
+      } else {
+        tp = 1.0;
+        tm = ratio_t(pos, neg);
+      }
+    }
+    double dh[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) dh[i] = tp * dp[i] - tm * dn[i];
+    // inverse of the midpoint map of limwd_body: dh0 = (u1 + u2)/2, dh1 = (u2 - u1)/2
+    *u1 = dh[0] - dh[1];
+    *u2 = dh[0] + dh[1];
+    return;
+  }
   T pos = 0, neg = 0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -1090,14 +1120,8 @@ __device__ __noinline__ void limiter_rebuild(const T d0, const T d1, const T d2,
   T dh[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) dh[i] = tp * (d[i] > T(0) ? d[i] : T(0)) - tm * (d[i] < T(0) ? -d[i] : T(0));
-  if constexpr (sizeof(T) == sizeof(double)) {
-    // inverse of the midpoint map above: dh0 = (u1 + u2)/2, dh1 = (u2 - u1)/2
-    *u1 = dh[0] - dh[1];
-    *u2 = dh[0] + dh[1];
-  } else {
-    *u1 = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) * tb.lim_idet);
-    *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) * tb.lim_idet);
-  }
+  *u1 = to_d<T>((dh[0] * tb.phm[1][2] - tb.phm[0][2] * dh[1]) * tb.lim_idet);
+  *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) * tb.lim_idet);
 }
 
 template <int P, typename T>
