@@ -1427,7 +1427,7 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
 // held to 3 (p = 1) or 2 (p = 2) resident 256-thread blocks per SM: left free, the union of the
 // phases takes more registers than any phase needs and only 2 blocks fit.
 template <int P, typename T>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 4 : 2) : 1)) k_ens_persistent(const EnsArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 5 : 2) : 1)) k_ens_persistent(const EnsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   __shared__ MemberDev sd;
@@ -1452,7 +1452,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 4 : 2) : 1)) 
 
 // The same phases as separate launches (one tile per block); the stream orders them.
 template <int P, typename T>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 4 : 2) : 1)) k_ens_phase(const EnsArgs a, int phase, int stage) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 5 : 2) : 1)) k_ens_phase(const EnsArgs a, int phase, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   __shared__ MemberDev sd;
