@@ -83,6 +83,9 @@ extern "C" {
                                   are staged in shared memory, every edge touching the tile is
                                   computed once by the block (edges between tiles by both), then
                                   each thread finishes its element (no flux scratch in HBM) */
+#define DGSWEM_VARIANT_TILED_WIDE 4 /* TILED with a tighter register bound in the FP32-mixed form
+                                       at p = 1 (5 instead of 4 resident 256-thread blocks per
+                                       SM): better on large meshes; identical to TILED otherwise */
 
 typedef struct dgswem_ctx dgswem_ctx; /* opaque, library-owned */
 

@@ -293,9 +293,9 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
     sa.rcdt = sa.rc * c->dt;
     sa.rk_form = rk_form_of(sa.ra, sa.rb, sa.rc);
     sa.err = c->err;
-    if (variant == DGSWEM_VARIANT_TILED) {
+    if (variant == DGSWEM_VARIANT_TILED || variant == DGSWEM_VARIANT_TILED_WIDE) {
       mark(c, kname_element, names, &ev_i);
-      launch_tile(c->mixed, c->P, false, c->dm, c->tiles, sa, ph, cfg);
+      launch_tile(c->mixed, c->P, variant == DGSWEM_VARIANT_TILED_WIDE, false, c->dm, c->tiles, sa, ph, cfg);
     } else {
       if (split && c->dm.nint > 0) {
         mark(c, kname_edge, names, &ev_i);
@@ -332,7 +332,7 @@ static void destroy_graph(dgswem_ctx *c) {
 
 int capture_graph(dgswem_ctx *c, int variant, int block, bool timing) {
   destroy_graph(c);
-  if (!c->ensemble && variant == DGSWEM_VARIANT_TILED)
+  if (!c->ensemble && (variant == DGSWEM_VARIANT_TILED || variant == DGSWEM_VARIANT_TILED_WIDE))
     if (int r = prepare_tiles(c, block)) return r;
   std::vector<const char *> names;
   if (timing) {
@@ -445,7 +445,7 @@ int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_par
   dgswem_ctx *c = new dgswem_ctx();
   c->prm = *params;
   if (tuning) c->tun = *tuning;
-  if (c->tun.variant < 0 || c->tun.variant > 3 || (c->tun.block != 0 && c->tun.block != 64 && c->tun.block != 128 &&
+  if (c->tun.variant < 0 || c->tun.variant > DGSWEM_VARIANT_TILED_WIDE || (c->tun.block != 0 && c->tun.block != 64 && c->tun.block != 128 &&
                                                     c->tun.block != 256) ||
       c->tun.reorder < 0 || c->tun.reorder > 2) {
     delete c;
@@ -497,10 +497,13 @@ static int upload_static(dgswem_ctx *c) {
 
 static int autotune(dgswem_ctx *c, int *best_variant, int *best_block) {
   std::vector<int> variants, blocks;
-  if (c->tun.variant == DGSWEM_VARIANT_AUTO)
+  if (c->tun.variant == DGSWEM_VARIANT_AUTO) {
     variants = {DGSWEM_VARIANT_SPLIT, DGSWEM_VARIANT_FUSED, DGSWEM_VARIANT_TILED};
-  else
+    // the wider register bound differs only for the float form at p = 1
+    if (c->mixed && c->P == 1) variants.push_back(DGSWEM_VARIANT_TILED_WIDE);
+  } else {
     variants = {c->tun.variant};
+  }
   if (c->tun.block == 0)
     blocks = {64, 128, 256};
   else
@@ -750,8 +753,8 @@ int dgswem_eval_rhs(dgswem_ctx *c, double t, double *h_out) {
   sa.err = c->err;
   sa.tide_t = t;
   const bool split = c->variant == DGSWEM_VARIANT_SPLIT;
-  if (c->variant == DGSWEM_VARIANT_TILED) {
-    launch_tile(c->mixed, c->P, true, c->dm, c->tiles, sa, c->ph, cfg);
+  if (c->variant == DGSWEM_VARIANT_TILED || c->variant == DGSWEM_VARIANT_TILED_WIDE) {
+    launch_tile(c->mixed, c->P, c->variant == DGSWEM_VARIANT_TILED_WIDE, true, c->dm, c->tiles, sa, c->ph, cfg);
   } else {
     if (split) launch_edge(c->mixed, c->P, c->dm, sa, c->ph, cfg);
     launch_element(c->mixed, c->P, split, true, c->dm, sa, c->ph, cfg);

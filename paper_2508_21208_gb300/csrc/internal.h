@@ -241,7 +241,7 @@ struct LaunchCfg {
   void launch_limwd_##SUF(int p, bool do_lim, int do_wd, const DevMesh &m, double *u,            \
                           const double *mean, uint8_t *wd, const Phys &ph, int *err,             \
                           const LaunchCfg &c);                                                   \
-  void launch_tile_##SUF(int p, bool write_rhs, const DevMesh &m, const DevTiles &tl,              \
+  void launch_tile_##SUF(int p, bool wide, bool write_rhs, const DevMesh &m, const DevTiles &tl,   \
                          const StageArgs &s, const Phys &ph, const LaunchCfg &c);                 \
   void prepare_tile_##SUF();                                                                      \
   cudaError_t launch_ensemble_##SUF(int p, bool persistent, const EnsArgs &a, int block, int grid, \
@@ -271,9 +271,9 @@ inline void launch_limwd(bool mixed, int p, bool do_lim, int do_wd, const DevMes
   mixed ? launch_limwd_f32(p, do_lim, do_wd, m, u, mean, wd, ph, err, c)
         : launch_limwd_f64(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
 }
-inline void launch_tile(bool mixed, int p, bool write_rhs, const DevMesh &m, const DevTiles &tl,
+inline void launch_tile(bool mixed, int p, bool wide, bool write_rhs, const DevMesh &m, const DevTiles &tl,
                         const StageArgs &s, const Phys &ph, const LaunchCfg &c) {
-  mixed ? launch_tile_f32(p, write_rhs, m, tl, s, ph, c) : launch_tile_f64(p, write_rhs, m, tl, s, ph, c);
+  mixed ? launch_tile_f32(p, wide, write_rhs, m, tl, s, ph, c) : launch_tile_f64(p, wide, write_rhs, m, tl, s, ph, c);
 }
 inline cudaError_t launch_ensemble(bool mixed, int p, bool persistent, const EnsArgs &a, int block, int grid,
                                    cudaStream_t s) {

@@ -1026,8 +1026,10 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
   __syncthreads();  // the shared-memory tile is reused by the block's next tile
 }
 
-template <int P, typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (P == 1 ? 4 : 2) : 1)
+// WIDE: the float form at p = 1 held to 48 registers (5 resident 256-thread blocks per SM instead
+// of 4): more latency hiding on large meshes, a nearly empty second wave on small ones.
+template <int P, typename T, bool WIDE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (P == 1 ? (WIDE ? 5 : 4) : 2) : 1)
     k_tile(const DevMesh m, const DevTiles tl, const StageArgs s, const Phys ph, const int write_rhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
@@ -1551,23 +1553,32 @@ void launch_element_t(int p, bool split, bool write_rhs, const DevMesh &m, const
 }
 
 template <typename T>
-void launch_tile_t(int p, bool write_rhs, const DevMesh &m, const DevTiles &tl, const StageArgs &s, const Phys &ph,
-                   const LaunchCfg &c) {
+void launch_tile_t(int p, bool wide, bool write_rhs, const DevMesh &m, const DevTiles &tl, const StageArgs &s,
+                   const Phys &ph, const LaunchCfg &c) {
   const int wr = write_rhs ? 1 : 0;
   if (p == 1) {
     const size_t sm = tile_smem_bytes<1, T>(tl.tile);
-    k_tile<1, T><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
+    if constexpr (sizeof(T) == sizeof(float)) {
+      if (wide) {
+        k_tile<1, T, true><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
+        return;
+      }
+    }
+    k_tile<1, T, false><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
   } else {
     const size_t sm = tile_smem_bytes<2, T>(tl.tile);
-    k_tile<2, T><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
+    k_tile<2, T, false><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
   }
 }
 
 template <typename T>
 void prepare_tile_t() {
   // allow the largest tile's dynamic shared memory (p = 2, 256 elements)
-  cudaFuncSetAttribute(k_tile<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256));
-  cudaFuncSetAttribute(k_tile<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256));
+  cudaFuncSetAttribute(k_tile<1, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256));
+  if constexpr (sizeof(T) == sizeof(float))
+    cudaFuncSetAttribute(k_tile<1, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tile_smem_bytes<1, T>(256));
+  cudaFuncSetAttribute(k_tile<2, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256));
   cudaFuncSetAttribute(k_ens_persistent<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)tile_smem_bytes<1, T>(256));
   cudaFuncSetAttribute(k_ens_persistent<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -26,9 +26,9 @@ cudaError_t launch_ensemble_f64(int p, bool persistent, const EnsArgs &a, int bl
 }
 int ensemble_blocks_per_sm_f64(int p, int block) { return ensemble_blocks_per_sm_t<double>(p, block); }
 
-void launch_tile_f64(int p, bool write_rhs, const DevMesh &m, const DevTiles &tl, const StageArgs &s,
+void launch_tile_f64(int p, bool wide, bool write_rhs, const DevMesh &m, const DevTiles &tl, const StageArgs &s,
                      const Phys &ph, const LaunchCfg &c) {
-  launch_tile_t<double>(p, write_rhs, m, tl, s, ph, c);
+  launch_tile_t<double>(p, wide, write_rhs, m, tl, s, ph, c);
 }
 void prepare_tile_f64() { prepare_tile_t<double>(); }
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libdgswem.so")
 DGSWEM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "EMESH", -3: "ECUDA", -4: "ENONFINITE", -5: "ENEGDEPTH", -6: "ETIMEOUT",
           -7: "ENOMEM", -8: "ESTATE", -9: "ETOOBIG"}
-VARIANT_AUTO, VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED = 0, 1, 2, 3
+VARIANT_AUTO, VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED, VARIANT_TILED_WIDE = 0, 1, 2, 3, 4
 ENSEMBLE_PERSISTENT, ENSEMBLE_PHASED = 1, 2
 FLUX_LLF, FLUX_ROE = 0, 1
 FP64, FP32_MIXED = 0, 1

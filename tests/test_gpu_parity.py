@@ -245,8 +245,25 @@ def test_full_size_shelf_parity_bench_config():
     g = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal)
     o = oracle.Oracle(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, omp=True)
     assert g.dt == pytest.approx(o.dt, rel=1e-14)
+    # the autotuner settled on a concrete organisation and timed every FP64 candidate
+    assert g.graph_info()[1] in (VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED)
+    assert sorted({v for v, _, _ in g.tune_log()}) == [VARIANT_SPLIT, VARIANT_FUSED, VARIANT_TILED]
     g.step(6)
     o.step(6)
     err = rel_l2(g.state(), o.state())
     assert np.all(err <= TOL), err
     assert np.array_equal(g.flags(), o.flags())
+
+
+def test_wide_tiled_variant_mixed_storm():
+    """The tighter-register-bound tile kernel (FP32-mixed, p = 1) computes what the tiled one does."""
+    from paper_2508_21208_gb300.dgswem import VARIANT_TILED_WIDE
+    c = synth.config3(n=40, precision=synth.FP32_MIXED)
+    a = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, variant=VARIANT_TILED, block=256)
+    b = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, variant=VARIANT_TILED_WIDE, block=256)
+    a.step(50)
+    b.step(50)
+    assert b.graph_info()[1] == VARIANT_TILED_WIDE
+    ua, ub = a.state(), b.state()
+    assert np.abs(ub[1:]).max() > 1e-4
+    assert np.abs(ua - ub).max() <= 1e-9 * max(1.0, np.abs(ua).max())
