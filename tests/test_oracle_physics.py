@@ -149,6 +149,33 @@ def test_quadratic_friction_matches_scalar_rk2():
     assert abs(q[0] - 1.0) > 1e-3  # friction did act
 
 
+def test_manning_friction_matches_scalar_rk2():
+    """Manning's law tau_b = g n^2 |q| / H^(7/3) on a uniform flow (Sec. 2.1, Eq. SWE friction term)
+    against the same SSP-RK2 written out by hand."""
+    n, H, g = 0.02, 10.0, 9.81
+    mesh, hb, init, prm = _uniform_case(dict(friction=synth.FRICTION_MANNING, manning_n=n, dt=5.0), (1.0, -0.5))
+
+    def f(q):
+        return -g * n * n * np.hypot(*q) * q / H ** (7.0 / 3.0)
+
+    def rk2(q, dt, k):
+        q1 = q + dt * f(q)
+        return q1, 0.5 * q + 0.5 * (q1 + dt * f(q1))
+
+    o = _run_with_exact_ghost(mesh, hb, init, prm, rk2, 40)
+    q = np.array([1.0, -0.5])
+    for k in range(40):
+        q = rk2(q, 5.0, k)[1]
+    u = o.state()
+    assert np.allclose(u[1, 0], q[0], rtol=1e-13, atol=0)
+    assert np.allclose(u[2, 0], q[1], rtol=1e-13, atol=0)
+    assert abs(q[0] - 1.0) > 1e-3  # friction did act
+    # Manning and quadratic friction agree when C_f = g n^2 / H^(1/3)
+    prm_q = dict(prm, friction=synth.FRICTION_QUADRATIC, cf=g * n * n / H ** (1.0 / 3.0))
+    oq = _run_with_exact_ghost(mesh, hb, init, prm_q, rk2, 40)
+    assert np.allclose(oq.state()[1:, 0], u[1:, 0], rtol=1e-12, atol=0)
+
+
 def test_coriolis_rotation_matches_rk2_amplification():
     lat = 28.0
     f = 2 * 7.2921e-5 * math.sin(math.radians(lat))
