@@ -4,8 +4,9 @@
  * The library advances the p-th order modal discontinuous Galerkin discretisation of the 2D
  * shallow water equations (Wichitrnithed et al., arXiv 2508.21208, Sec. 2.1 Eq. SWE and
  * Sec. 2.2 Eq. elem_weak_form / Eq. RKSSP) on an unstructured triangle mesh on one GPU:
- * area integrals of flux and sources (Alg. 1), interior, land and open-ocean edge fluxes
- * (Alg. 2, Alg. 3), the inverse (diagonal) mass matrix and the SSP-RK2 stage update, the slope
+ * area integrals of flux and sources (Alg. 1), interior, land, open-ocean and river edge fluxes
+ * (Alg. 2, Alg. 3; LLF or Roe), the inverse (diagonal) mass matrix and the SSP-RK stage update
+ * (SSP-RK2 by default), the slope
  * limiter and the wetting/drying treatment (Sec. 5.2.3 SLOPELIM, WETDRY), and nodal wind /
  * pressure forcing (Sec. 5.2.3 WIND).  Every step runs in CUDA kernels built for sm_103a; there
  * is no CPU fallback.  Host code only preprocesses the mesh (edge list, neighbour maps, limiter
@@ -182,8 +183,8 @@ DGSWEM_API int dgswem_workspace_size(const dgswem_ctx *ctx, size_t *bytes);
  * Errors: DGSWEM_ENOMEM, DGSWEM_ECUDA, DGSWEM_ESTATE (already attached). */
 DGSWEM_API int dgswem_attach(dgswem_ctx *ctx, void *d_workspace, size_t bytes, void *stream);
 
-/* Advance n_steps SSP-RK2 time steps (two stages each, Sec. 2.2 Eq. RKSSP) by replaying the
- * captured graph.  Asynchronous: device-side errors (DGSWEM_ENONFINITE, DGSWEM_ENEGDEPTH) are
+/* Advance n_steps time steps of the chosen SSP-RK scheme (Sec. 2.2 Eq. RKSSP; SSP-RK2 by
+ * default) by replaying the captured graph.  Asynchronous: device-side errors (DGSWEM_ENONFINITE, DGSWEM_ENEGDEPTH) are
  * reported by the next synchronising call. */
 DGSWEM_API int dgswem_step(dgswem_ctx *ctx, int32_t n_steps);
 

@@ -259,7 +259,7 @@ static void mark(dgswem_ctx *c, const char *name, std::vector<const char *> *nam
   ++*ev_i;
 }
 
-// Issue the kernels of one time step (two SSP-RK2 stages) on the context stream.
+// Issue the kernels of one time step (the scheme's stages) on the context stream.
 static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const char *> *names) {
   const bool split = variant == DGSWEM_VARIANT_SPLIT;
   const LaunchCfg cfg{block, c->st};

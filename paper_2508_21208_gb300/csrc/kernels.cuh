@@ -1,5 +1,5 @@
 // kernels.cuh -- device code of one RK stage: forcing (WIND), edge flux (EDGE), element update
-// (AREA + GATHER + inverse mass + SSP-RK2), slope limiter + wetting/drying (SLOPELIM, WETDRY).
+// (AREA + GATHER + inverse mass + SSP-RK stage), slope limiter + wetting/drying (SLOPELIM, WETDRY).
 // Included by kernels_f64.cu (T = double: the FP64 form) and kernels_f32.cu (T = float: the
 // mixed form, where the RK state, the RK update and all wet/dry depth tests stay in double).
 #pragma once
@@ -496,8 +496,9 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
 // ------------------------------------------------------------------------ element update
 // One thread per element.  r_k = (grad phi_k, F)_e + (phi_k, s)_e - <phi_k, Fhat.n>_de
 // (Eq. elem_weak_form with the volume term's sign fixed by integration by parts, Alg. 1 and the
-// gather of Alg. 3), L_k = r_k / (|J| ||phi_k||^2), then the SSP-RK2 stage (Shu-Osher form):
-// stage 0: u1 = u + dt L(u); stage 1: u_new = u/2 + (u1 + dt L(u1))/2, in double.
+// gather of Alg. 3), L_k = r_k / (|J| ||phi_k||^2), then the SSP-RK stage in the two-register
+// Shu-Osher form u_out = a u^n + b u_in + c dt L(u_in), in double (SSP-RK2: u1 = u + dt L(u),
+// then u_new = (u + (u1 + dt L(u1)))/2).
 // Source terms linear in the state (bathymetry slope g zeta dh_b/dx, Coriolis, wind stress,
 // pressure gradient -H dp_a/dx with linear p_a) are integrated in closed form through the basis
 // orthogonality; the area rule is exact for them, so this is the same discrete operator.
