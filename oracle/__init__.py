@@ -6,8 +6,8 @@ CPU-baseline leg of ``bench.py`` may import this package.  The product
 
 The C source follows the paper's Sec. 2 (model and DG formulation) and
 Algorithms 1-3 (AREA, EDGE, GATHER); see its header for the readings taken
-where the paper is silent.  Parity unpinned: the slope limiter and the
-wet/dry treatment are checked only through invariants.
+where the paper is silent.  Partly pinned: the slope limiter and the wet/dry
+treatment are checked through invariants and one hand-worked example each.
 """
 from __future__ import annotations
 

@@ -49,7 +49,7 @@
  *     shifted so that the mean normal discharge of the two traces is the inflow -q_in;
  *   - rain R (Eq. SWE): a uniform rate in the continuity equation;
  *   - hurricane: Holland (1980) pressure and gradient wind, Garratt (1977) drag.
- * Parity unpinned: slope limiter and wet/dry (pinned only by invariants).
+ * Partly pinned: slope limiter and wet/dry (invariants and one hand-worked example each).
  *
  * Compile: gcc -O2 -ffp-contract=off -fPIC -shared (optionally -fopenmp).
  */

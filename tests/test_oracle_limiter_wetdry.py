@@ -1,7 +1,6 @@
-"""Invariants that pin the oracle's slope limiter and wet/dry operator (Sec. 5.2.3 SLOPELIM,
-WETDRY).  The paper does not define either operator, so beyond these properties their parity is
-unpinned: the limiter is the Cockburn-Shu triangle minmod limiter, the wet/dry step a
-mean-preserving vertex-depth fix.  Vertex values are evaluated here with scipy's Jacobi
+"""Invariants and hand-worked examples that pin the oracle's slope limiter and wet/dry operator
+(Sec. 5.2.3 SLOPELIM, WETDRY).  The paper does not define either operator: the limiter is the
+Cockburn-Shu triangle minmod limiter, the wet/dry step a mean-preserving vertex-depth fix.  Vertex values are evaluated here with scipy's Jacobi
 polynomials, independently of the oracle's basis code."""
 import numpy as np
 import pytest
@@ -136,3 +135,83 @@ def test_initial_shelf_state_dry_land_at_h0():
     assert np.all(f[land] == 2)
     assert np.all(f[sea] == 0)
     assert cx[f == 2].min() > 90e3
+
+
+# ---------------------------------------------------------------- hand-worked examples
+def _modes_from_vertices(a0, a1, a2):
+    """Linear Dubiner modes of the interpolant through vertex values (a0, a1, a2): the mean, then
+    psi_10 and psi_01 coefficients (psi_10 = -1, 1, 0 and psi_01 = -1, -1, 2 at the vertices)."""
+    return np.array([(a0 + a1 + a2) / 3.0, 0.5 * (a1 - a0), (2.0 * a2 - a0 - a1) / 6.0])
+
+
+def _vertices_from_modes(m):
+    return np.array([m[0] - m[1] - m[2], m[0] + m[1] - m[2], m[0] + 2.0 * m[2]])
+
+
+def test_limiter_worked_example():
+    """Cockburn-Shu limiting of one element, worked by hand.
+
+    Four triangles split the triangle (0,0), (2,0), (0,2) at its edge midpoints D(1,0), E(1,1),
+    F(0,1); the centre element DEF has neighbours DBE, FEC, ADF across DE, EF, FD.  Each midpoint
+    of the centre, measured from its barycentre (2/3, 2/3), is half the vector to the barycentre
+    of the neighbour across that edge, so the neighbour-mean difference at each midpoint is half
+    the difference of the means.
+
+    Centre: mean 1, vertex values D 1.2, E 1.4, F 0.4, i.e. midpoint deviations 0.3 (DE), -0.1 (EF),
+    -0.2 (FD).  Neighbour means: DBE 1.2, FEC 0.7, ADF 0.9, i.e. differences 0.1, -0.15, -0.05.
+    minmod(deviation, 1.5 x difference): 0.15, -0.1, -0.075; their sum -0.025 != 0, so the
+    negative ones are scaled by 0.15 / 0.175 = 6/7: 0.15, -0.6/7, -0.45/7.  The limited vertex
+    values follow: D = 1 + 1.2/7, E = 1 + 0.9/7, F = 0.7.
+    """
+    xy = np.array([[0, 0], [2, 0], [0, 2], [1, 0], [1, 1], [0, 1]], float) * 1000.0
+    tri = np.array([[3, 4, 5], [0, 3, 5], [3, 1, 4], [5, 4, 2]], np.int32)
+    bedge = np.array([[0, 3], [3, 1], [1, 4], [4, 2], [2, 5], [5, 0]], np.int32)
+    mesh = synth.Mesh(xy, tri, bedge, np.zeros(6, np.int32))
+    hb = np.full(6, 10.0)
+    prm = synth.default_params(limiter=1)
+    u = np.zeros((3, 3, 4))
+    u[0, :, 0] = _modes_from_vertices(1.2, 1.4, 0.4)
+    u[0, 0, 1], u[0, 0, 2], u[0, 0, 3] = 0.9, 1.2, 0.7  # ADF, DBE, FEC: means only
+    o = oracle.Oracle(mesh, hb, prm, init_modal=u)
+    o.set_state(u)
+    o.apply_limiter()
+    got = _vertices_from_modes(o.state()[0, :, 0])
+    assert np.allclose(got, [1.0 + 1.2 / 7.0, 1.0 + 0.9 / 7.0, 0.7], rtol=0, atol=1e-14)
+    assert o.state()[0, 0, 0] == pytest.approx(1.0, abs=1e-15)  # mean kept
+    # the same element with every deviation inside the neighbour bounds is left alone
+    u2 = u.copy()
+    u2[0, :, 0] = _modes_from_vertices(1.04, 1.06, 0.9)  # deviations 0.05, -0.02, -0.03
+    o.set_state(u2)
+    o.apply_limiter()
+    assert np.allclose(o.state()[0, :, 0], u2[0, :, 0], rtol=0, atol=1e-15)
+
+
+def test_wetdry_worked_example():
+    """The wetting/drying operator on one element, worked by hand (h0 = 0.01 m).
+
+    Vertex depths (0.005, 0.02, 0.05): mean 0.025 > h0, vertex 0 lifted to h0, the others' excess
+    over h0 (0.01, 0.04) scaled by 3 (0.025 - 0.01) / 0.05 = 0.9 to keep the mean:
+    (0.01, 0.019, 0.046).  The element is partially wet; with beds (-0.5, 0.3, 1.0) the mean
+    surface (-0.2417 m) lies below the highest bed among the vertices at h0 (0.5 m, vertex 0), so
+    its momentum is removed.  Vertex depths (0.002, 0.004, 0.006): mean 0.004 <= h0, dry: flat at
+    0.004 with no momentum.
+    """
+    xy = np.array([[0.0, 0.0], [1000.0, 0.0], [0.0, 1000.0]])
+    mesh = synth.Mesh(xy, np.array([[0, 1, 2]], np.int32), np.array([[0, 1], [1, 2], [2, 0]], np.int32),
+                      np.zeros(3, np.int32))
+    hb = np.array([-0.5, 0.3, 1.0])
+    prm = synth.default_params(h0=0.01)
+    for H, expect, flag in (((0.005, 0.02, 0.05), (0.01, 0.019, 0.046), 1),
+                            ((0.002, 0.004, 0.006), (0.004, 0.004, 0.004), 2)):
+        u = np.zeros((3, 3, 1))
+        u[0, :, 0] = _modes_from_vertices(*(np.array(H) - hb))
+        u[1, :, 0] = [0.3, 0.01, -0.02]
+        u[2, :, 0] = [-0.1, 0.0, 0.03]
+        o = oracle.Oracle(mesh, hb, prm, init_modal=u)
+        o.set_state(u)
+        o.apply_wetdry()
+        s = o.state()
+        got = _vertices_from_modes(s[0, :, 0]) + hb
+        assert np.allclose(got, expect, rtol=0, atol=1e-15), (H, got)
+        assert o.flags()[0] == flag
+        assert np.all(s[1:] == 0.0)
