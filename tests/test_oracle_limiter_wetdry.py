@@ -215,3 +215,30 @@ def test_wetdry_worked_example():
         assert np.allclose(got, expect, rtol=0, atol=1e-15), (H, got)
         assert o.flags()[0] == flag
         assert np.all(s[1:] == 0.0)
+
+
+def test_wetdry_edge_rule_worked_example():
+    """The edge rule between a wet and a dry element (reading of Sec. 5.2.2): the edge carries no
+    flow unless the wet side's surface at the edge's Gauss points rises above the edge's highest
+    bed.  Two triangles share the diagonal (1000, 0)-(0, 1000) of a square; the dry one (upper
+    right) is land up to 1 m above the datum (h_b = -1 there, -0.6 on the shared edge), water at
+    h0.  The wet one (lower left) is level at its mean surface zeta_A: below the highest bed on
+    the edge (0.6 m), no mass reaches the dry element; above it, mass flows in."""
+    xy = np.array([[0.0, 0.0], [1000.0, 0.0], [0.0, 1000.0], [1000.0, 1000.0]])
+    tri = np.array([[0, 1, 2], [1, 3, 2]], np.int32)
+    bedge = np.array([[0, 1], [1, 3], [3, 2], [2, 0]], np.int32)
+    mesh = synth.Mesh(xy, tri, bedge, np.zeros(4, np.int32))
+    hb = np.array([5.0, -0.6, -0.6, -1.0])
+    prm = synth.default_params(h0=0.01)
+    for zeta_a, flows in ((0.4, False), (0.9, True)):
+        u = np.zeros((3, 3, 2))
+        u[0, 0, 0] = zeta_a                                   # wet, level
+        u[0, :, 1] = _modes_from_vertices(*(0.01 - hb[[1, 3, 2]]))  # dry, water at h0
+        o = oracle.Oracle(mesh, hb, prm, init_modal=u)
+        o.set_state(u)
+        assert list(o.flags()) == [1, 2] or list(o.flags()) == [0, 2]
+        L = o.rhs(0.0)
+        if flows:
+            assert L[0, 0, 1] > 1e-6 and L[0, 0, 0] < -1e-9   # mass leaves A, enters B
+        else:
+            assert L[0, 0, 1] == 0.0 and abs(L[0, 0, 0]) < 1e-15
