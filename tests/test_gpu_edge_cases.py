@@ -93,3 +93,36 @@ def test_zero_steps_leaves_state_unchanged():
     g.step(0)
     assert np.array_equal(g.state(), u0)
     assert g.info()[2] == 0
+
+
+def test_blow_up_is_reported_and_sticky():
+    """A time step 50x the CFL limit blows the solution up; the kernels' finiteness checks turn
+    that into DGSWEM_ENONFINITE at the next synchronising call, and the context stays failed."""
+    from paper_2508_21208_gb300.dgswem import DgswemError
+    c = synth.config1()
+    g0 = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal)
+    prm = dict(c.params)
+    prm["dt"] = 50.0 * g0.dt
+    g = Model(c.mesh, c.bathy, prm, init_nodal=c.init_nodal)
+    with pytest.raises(DgswemError) as ei:
+        g.step(200)
+        g.sync()
+    assert ei.value.code == -4
+    with pytest.raises(DgswemError):
+        g.state()
+
+
+def test_negative_mean_depth_is_reported():
+    """A state whose mean depth is negative cannot be repaired by the wet/dry operator: it
+    reports DGSWEM_ENEGDEPTH instead of continuing."""
+    from paper_2508_21208_gb300.dgswem import DgswemError
+    c = synth.config2(n=16)
+    g = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal)
+    u = g.state()
+    hbm = c.bathy[c.mesh.tri].mean(axis=1)
+    u[0, 0, 5] = -hbm[5] - 1.0  # 1 m below the bed
+    with pytest.raises(DgswemError) as ei:
+        g.set_state(u)  # classifies the state (may already report it)
+        g.apply_wetdry()
+        g.sync()
+    assert ei.value.code == -5
