@@ -213,7 +213,31 @@ def cpu_baseline(case, budget_s=12.0):
     el1 = time.perf_counter() - t1
     out["single_thread"] = {"value": case.mesh.n_elems * 2 * n1 / el1, "unit": UNIT, "cores": 1,
                             "sample": f"{n1} steps of the same workload ({el1:.1f} s, serial build)"}
+    out["other_workloads"] = oracle_other_workloads()
     return out
+
+
+def oracle_other_workloads(budget_s=2.5):
+    """The OpenMP oracle on the other workloads, a bounded number of steps each (at least one)."""
+    import oracle
+    from paper_2508_21208_gb300 import synth
+    cases = [("800-triangle basin (Manning)", synth.config1()),
+             ("storm 3,200,450 elements (FP64, hurricane, Coriolis)", synth.config3())]
+    meshes, bathys, members = synth.ensemble(members_per_mesh=1, precision=synth.FP64)
+    for mi, (mesh, hb) in enumerate(zip(meshes, bathys)):
+        cases.append((f"ensemble mesh {mesh.n_elems} elements (one storm)",
+                      synth.Case("ens", mesh, hb, np.zeros((3, mesh.n_nodes)), members[mi][1], 1)))
+    res = {}
+    for name, c in cases:
+        o = oracle.Oracle(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, omp=True)
+        n, t0 = 0, time.perf_counter()
+        while n == 0 or (time.perf_counter() - t0 < budget_s and n < 200):
+            o.step(1)
+            n += 1
+        el = time.perf_counter() - t0
+        res[name] = {"value": c.mesh.n_elems * 2 * n / el, "unit": UNIT, "steps": n, "seconds": round(el, 2)}
+        del o
+    return res
 
 
 def e2e(case, steps, stream):
