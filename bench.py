@@ -96,8 +96,10 @@ class ClockSampler:
 
 
 def kernel_source_sha():
+    """Hash of the device code and of what shapes its data (kernel sources and instantiations,
+    the structs passed to kernels, the mesh preprocessing that builds tables and tile lists)."""
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "common_kernels.cu", "api.cu"):
+    for f in ("kernels.cuh", "kernels_f64.cu", "kernels_f32.cu", "common_kernels.cu", "internal.h", "mesh.cu"):
         h.update(open(os.path.join(ROOT, "paper_2508_21208_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -150,22 +152,39 @@ def make_model(case, stream, **kw):
     return Model(case.mesh, case.bathy, case.params, init_nodal=case.init_nodal, stream=stream, **kw)
 
 
+KERNEL_TIMING_EVERY = 10
+
+
+def kernel_timed_steps(steps):
+    return (steps + KERNEL_TIMING_EVERY - 1) // KERNEL_TIMING_EVERY
+
+
 def time_steps(model, steps, warmup, stream, flush, per_kernel=False):
-    """Per-step CUDA-event timing on the library's stream, L2 flushed between steps."""
+    """Per-step CUDA-event timing on the library's stream, L2 flushed between steps.
+
+    With per_kernel, every KERNEL_TIMING_EVERY-th timed step replays the graph variant with
+    event-record nodes between its kernels, whose per-kernel durations are collected; the
+    other steps replay the plain graph (the event nodes lengthen a step by a few microseconds)."""
     import torch
     for _ in range(warmup):
         model.step(1)
     model.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     kt = {}
+    if per_kernel:  # capture both graphs before the timed region
+        model.set_kernel_timing(True)
+        model.set_kernel_timing(False)
     torch.cuda.profiler.start()  # an ncu run with --profile-from-start off sees only these steps
     for i in range(steps):
+        timed = per_kernel and i % KERNEL_TIMING_EVERY == 0
+        if per_kernel:
+            model.set_kernel_timing(timed)
         with torch.cuda.stream(stream):
             flush.zero_()
         ev[i][0].record(stream)
         model.step(1)
         ev[i][1].record(stream)
-        if per_kernel:
+        if timed:
             stream.synchronize()
             for name, ms in model.kernel_times():
                 kt.setdefault(name, []).append(ms)
@@ -375,7 +394,7 @@ def main():
             "peak_kind": "derived from unit counts and clocks (FP64)",
             "frac": (flops / avg_s / 1e9) / FP64_PEAK_GFLOPS if flops else None,
             "traffic": recorded_traffic(name, "fp64", ne, variant),
-            "avg_launch_ms": avg_s * 1e3, "launches_per_step": len(kt[name]) // args.steps,
+            "avg_launch_ms": avg_s * 1e3, "launches_per_step": len(kt[name]) // kernel_timed_steps(args.steps),
             "share_of_step": tot[name] / sum(tot.values())}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -388,7 +407,7 @@ def main():
             "hbm_gbs_algorithmic": ALG_BYTES[("fp64", 1)] * value / world / 1e9,
             "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
             "roofline": roof,
-            "kernel_ms_per_step": {k: sum(v) / args.steps for k, v in kt.items()},
+            "kernel_ms_per_step": {k: sum(v) / kernel_timed_steps(args.steps) for k, v in kt.items()},
             "clocks": clk.summary()}
     if world == 1:
         line["e2e"] = e2e(case, max(10, args.steps // 4), stream)
@@ -414,7 +433,8 @@ def extras(stream, flush, hbm):
         gbs = ALG_BYTES[(form, p)] * rate / 1e9
         out[key] = {"value": rate, "unit": UNIT, "elements": case.mesh.n_elems, "ms_per_step": sum(ms) / 20,
                     "variant": variant, "block": block, "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm,
-                    "dominant_kernel": name, "kernel_ms_per_step": {k: sum(v) / 20 for k, v in kt.items()}}
+                    "dominant_kernel": name,
+                    "kernel_ms_per_step": {k: sum(v) / kernel_timed_steps(20) for k, v in kt.items()}}
         del m
     out["ensemble_64_storms"] = ensemble_form(stream)
     return out

@@ -14,7 +14,9 @@
  *
  * Conventions (all entry points):
  *  - Return 0 on success or a negative DGSWEM_E* code.  Errors are sticky per context; the text
- *    of the first one is available from dgswem_last_error().
+ *    of the first one is available from dgswem_last_error().  The exception is a query the
+ *    context's mode cannot answer (dgswem_kernel_times with timing off): DGSWEM_ESTATE, not
+ *    sticky.
  *  - Pointers named h_* / plain const pointers are HOST memory owned by the caller and only read
  *    during the call (create deep-copies them).  The one device buffer the library uses is the
  *    workspace the caller attaches (dgswem_attach); the library allocates no device memory.
@@ -226,13 +228,17 @@ DGSWEM_API int dgswem_eval_rhs(dgswem_ctx *ctx, double t, double *h_out);
 DGSWEM_API int dgswem_apply_limiter(dgswem_ctx *ctx);
 /* Apply the wetting/drying operator (WETDRY) to the current state in place. */
 DGSWEM_API int dgswem_apply_wetdry(dgswem_ctx *ctx);
-/* Nodal forcing (WIND) at time t: h_out [3][n_nodes] = (tau_x/rho_w, tau_y/rho_w, p_a/rho_w). */
+/* Nodal forcing (WIND) at time t: h_out [3][n_nodes] = (tau_x/rho_w, tau_y/rho_w,
+ * (p_a - p_n)/rho_w); the pressure anomaly, since only its gradient enters Eq. SWE. */
 DGSWEM_API int dgswem_eval_forcing(dgswem_ctx *ctx, double t, double *h_out);
 
 /* ---- kernel timing ----
- * With timing on, the step graph is recaptured with event-record nodes between its kernels;
- * dgswem_kernel_times then returns, for the last replayed step, each kernel's duration in
- * milliseconds and its name (static strings), in launch order.  n_kernels gets the count. */
+ * With timing on, dgswem_step replays a graph of the same step with event-record nodes between
+ * its kernels (captured on first use; both graphs are kept, so switching back and forth costs a
+ * stream synchronisation only).  dgswem_kernel_times then returns, for the last replayed step,
+ * each kernel's duration in milliseconds and its name (static strings), in launch order;
+ * n_kernels gets the count.  The event nodes lengthen a step by a few microseconds, so a caller
+ * timing whole steps turns timing on only for the steps whose kernel times it reads. */
 DGSWEM_API int dgswem_set_kernel_timing(dgswem_ctx *ctx, int32_t on);
 DGSWEM_API int dgswem_kernel_times(dgswem_ctx *ctx, float *ms, const char **names, int32_t capacity,
                         int32_t *n_kernels);

@@ -25,6 +25,12 @@ int ctx_fail(dgswem_ctx *c, int code, const std::string &msg) {
   return code;
 }
 
+// A query the context's current mode cannot answer: reported, but not sticky.
+static int ctx_refuse(dgswem_ctx *c, int code, const std::string &msg) {
+  if (c && c->sticky == 0) c->errmsg = msg;
+  return code;
+}
+
 int ctx_cuda(dgswem_ctx *c, cudaError_t e, const char *what) {
   if (e == cudaSuccess) return 0;
   return ctx_fail(c, DGSWEM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -323,15 +329,24 @@ static int kernels_in_step(const dgswem_ctx *c, int variant) {
   return c->nst * per_stage + 1;
 }
 
+static void destroy_alt(dgswem_ctx *c) {
+  if (c->exec_alt) cudaGraphExecDestroy(c->exec_alt);
+  if (c->graph_alt) cudaGraphDestroy(c->graph_alt);
+  c->exec_alt = nullptr;
+  c->graph_alt = nullptr;
+}
+
 static void destroy_graph(dgswem_ctx *c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->exec = nullptr;
   c->graph = nullptr;
+  destroy_alt(c);
 }
 
-int capture_graph(dgswem_ctx *c, int variant, int block, bool timing) {
-  destroy_graph(c);
+// Capture one step for (variant, block) with or without the kernel-timing event nodes, as the
+// active graph (the caller has released the previous one).
+static int capture_one(dgswem_ctx *c, int variant, int block, bool timing) {
   if (!c->ensemble && (variant == DGSWEM_VARIANT_TILED || variant == DGSWEM_VARIANT_TILED_WIDE))
     if (int r = prepare_tiles(c, block)) return r;
   std::vector<const char *> names;
@@ -354,11 +369,14 @@ int capture_graph(dgswem_ctx *c, int variant, int block, bool timing) {
   c->variant = variant;
   c->block = block;
   c->timing = timing;
-  c->knames = names;
-  size_t nodes = 0;
-  cudaGraphGetNodes(c->graph, nullptr, &nodes);
+  if (timing) c->knames = names;
   c->kernels_per_step = c->ensemble ? c->kernels_per_step : kernels_in_step(c, variant);
   return 0;
+}
+
+int capture_graph(dgswem_ctx *c, int variant, int block, bool timing) {
+  destroy_graph(c);
+  return capture_one(c, variant, block, timing);
 }
 
 int read_error_word(dgswem_ctx *c) {
@@ -813,12 +831,28 @@ int dgswem_set_kernel_timing(dgswem_ctx *c, int32_t on) {
   if (c->sticky) return c->sticky;
   if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
   if (int r = ctx_cuda(c, cudaStreamSynchronize(c->st), "sync")) return r;
-  return capture_graph(c, c->variant, c->block, on != 0);
+  const bool want = on != 0;
+  if (want == c->timing && c->exec) return 0;
+  if (c->exec_alt && c->alt_timing == want) {  // the other mode is already captured: swap
+    std::swap(c->graph, c->graph_alt);
+    std::swap(c->exec, c->exec_alt);
+    c->alt_timing = c->timing;
+    c->timing = want;
+    return 0;
+  }
+  // keep the active graph as the alternative and capture the requested mode
+  destroy_alt(c);
+  c->graph_alt = c->graph;
+  c->exec_alt = c->exec;
+  c->alt_timing = c->timing;
+  c->graph = nullptr;
+  c->exec = nullptr;
+  return capture_one(c, c->variant, c->block, want);
 }
 
 int dgswem_kernel_times(dgswem_ctx *c, float *ms, const char **names, int32_t cap, int32_t *n) {
   if (!c || !n) return DGSWEM_EINVAL;
-  if (!c->timing) return ctx_fail(c, DGSWEM_ESTATE, "kernel timing is off");
+  if (!c->timing) return ctx_refuse(c, DGSWEM_ESTATE, "kernel timing is off");
   if (int r = ctx_cuda(c, cudaStreamSynchronize(c->st), "sync")) return r;
   const int k = (int)c->knames.size();
   *n = k;

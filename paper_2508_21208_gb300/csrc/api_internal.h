@@ -66,6 +66,10 @@ struct dgswem_ctx {
   cudaGraphExec_t exec = nullptr;
   int kernels_per_step = 0, variant = 0, block = 128;
   bool timing = false;
+  // the same configuration captured in the other timing mode, kept so that switching is free
+  cudaGraph_t graph_alt = nullptr;
+  cudaGraphExec_t exec_alt = nullptr;
+  bool alt_timing = false;
   std::vector<cudaEvent_t> ev;
   std::vector<const char *> knames;
   std::vector<TuneEntry> tune_log;

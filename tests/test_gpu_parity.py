@@ -267,3 +267,23 @@ def test_wide_tiled_variant_mixed_storm():
     ua, ub = a.state(), b.state()
     assert np.abs(ub[1:]).max() > 1e-4
     assert np.abs(ua - ub).max() <= 1e-9 * max(1.0, np.abs(ua).max())
+
+
+def test_kernel_timing_switch_keeps_results_bitwise():
+    """Switching the timed graph on and off (both kept captured) changes nothing in the results,
+    and per-kernel times are available exactly while timing is on."""
+    from paper_2508_21208_gb300.dgswem import DgswemError
+    c = synth.config2(n=40)
+    a = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, variant=VARIANT_TILED, block=128)
+    b = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, variant=VARIANT_TILED, block=128)
+    a.step(12)
+    for i in range(12):
+        b.set_kernel_timing(i % 3 == 0)
+        b.step(1)
+        if i % 3 == 0:
+            names = [n for n, _ in b.kernel_times()]
+            assert names.count("element_update") == 2 and "limiter_wetdry" in names
+        else:
+            with pytest.raises(DgswemError):
+                b.kernel_times()
+    assert np.array_equal(a.state(), b.state())
