@@ -129,3 +129,32 @@ def test_single_triangle_accepted(lib):
     rc, h = _create(_one_triangle([0.0, 1000.0]), np.full(3, 10.0), synth.config1(n=4).params)
     assert rc == 0 and h
     lib.dgswem_destroy(h)
+
+
+def _ens_create(lib, meshes, bathys, members):
+    marr = [dgswem._MeshArrays(m) for m in meshes]
+    hbs = [np.ascontiguousarray(b, np.float64) for b in bathys]
+    n = len(members)
+    mesh_ptrs = (C.POINTER(dgswem.Mesh) * n)()
+    hb_ptrs = (C.POINTER(C.c_double) * n)()
+    prms = (dgswem.Params * n)()
+    inits = (dgswem.Init * n)()
+    for i, (mi, prm) in enumerate(members):
+        mesh_ptrs[i] = C.pointer(marr[mi].s)
+        hb_ptrs[i] = dgswem._ptr(hbs[mi])
+        prms[i] = dgswem.make_params(prm)
+        inits[i] = dgswem.Init(None, None, 0.0)
+    h = C.c_void_p()
+    rc = lib.dgswem_ensemble_create(n, mesh_ptrs, hb_ptrs, prms, inits, C.byref(dgswem.Tuning(0, 0, 0, 0)), C.byref(h))
+    if rc == 0:
+        lib.dgswem_destroy(h)
+    return rc
+
+
+@pytest.mark.parametrize("key,val", [("p", 2), ("precision", synth.FP32_MIXED), ("rk_scheme", synth.RK_SSP33)])
+def test_ensemble_members_must_share_degree_precision_and_scheme(lib, key, val):
+    c = synth.config1(n=6)
+    other = dict(c.params)
+    other[key] = val
+    assert _ens_create(lib, [c.mesh], [c.bathy], [(0, c.params), (0, dict(c.params))]) == 0
+    assert _ens_create(lib, [c.mesh], [c.bathy], [(0, c.params), (0, other)]) == -1

@@ -283,6 +283,7 @@ def test_kernel_timing_switch_keeps_results_bitwise():
         if i % 3 == 0:
             names = [n for n, _ in b.kernel_times()]
             assert names.count("element_update") == 2 and "limiter_wetdry" in names
+            assert len(names) == b.graph_info()[0]  # the kernels-per-step count the bench reports
         else:
             with pytest.raises(DgswemError):
                 b.kernel_times()
