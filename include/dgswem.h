@@ -271,6 +271,10 @@ DGSWEM_API int dgswem_ensemble_create(int32_t n, const dgswem_mesh *const *meshe
                            const double *const *bathy, const dgswem_params *params,
                            const dgswem_init *inits, const dgswem_tuning *tuning,
                            dgswem_ctx **out);
+/* Advance every member n_steps of its own time step: dgswem_step on an ensemble context (one
+ * replay of the captured ensemble step per step), checked to be one.  DGSWEM_EINVAL for a
+ * single-model context or n_steps < 0. */
+DGSWEM_API int dgswem_ensemble_step(dgswem_ctx *ctx, int32_t n_steps);
 DGSWEM_API int dgswem_ensemble_get_state(dgswem_ctx *ctx, int32_t member, double *h_zeta, double *h_qx,
                               double *h_qy);
 DGSWEM_API int dgswem_ensemble_info(dgswem_ctx *ctx, int32_t member, double *dt, double *t,

@@ -436,6 +436,11 @@ int dgswem_ensemble_create(int32_t n, const dgswem_mesh *const *meshes, const do
   return 0;
 }
 
+int dgswem_ensemble_step(dgswem_ctx *c, int32_t n) {
+  if (!c || !c->ensemble) return DGSWEM_EINVAL;
+  return dgswem_step(c, n);
+}
+
 int dgswem_ensemble_get_state(dgswem_ctx *c, int32_t member, double *hz, double *hqx, double *hqy) {
   if (!c || !c->ensemble) return DGSWEM_EINVAL;
   if (c->sticky) return c->sticky;

@@ -89,6 +89,7 @@ SIGNATURES = [
                                   C.POINTER(C.c_int32)]),
     ("dgswem_ensemble_create", C.c_int, [C.c_int32, C.POINTER(C.POINTER(Mesh)), C.POINTER(_dp),
                                          C.POINTER(Params), C.POINTER(Init), C.POINTER(Tuning), C.POINTER(_vp)]),
+    ("dgswem_ensemble_step", C.c_int, [_vp, C.c_int32]),
     ("dgswem_ensemble_get_state", C.c_int, [_vp, C.c_int32, _dp, _dp, _dp]),
     ("dgswem_ensemble_info", C.c_int, [_vp, C.c_int32, _dp, _dp, C.POINTER(C.c_int64)]),
     ("dgswem_ensemble_set_fault", C.c_int, [_vp, C.c_int32]),
@@ -314,6 +315,9 @@ class Ensemble(_Handle):
         self.meshes = meshes
         self.nd = (members[0][1]["p"] + 1) * (members[0][1]["p"] + 2) // 2
         self._attach(stream)
+
+    def step(self, n: int = 1):
+        self._check(self.lib.dgswem_ensemble_step(self.h, int(n)))
 
     def state(self, i: int) -> np.ndarray:
         ne = self.meshes[self.members[i][0]].n_elems

@@ -158,3 +158,11 @@ def test_ensemble_members_must_share_degree_precision_and_scheme(lib, key, val):
     other[key] = val
     assert _ens_create(lib, [c.mesh], [c.bathy], [(0, c.params), (0, dict(c.params))]) == 0
     assert _ens_create(lib, [c.mesh], [c.bathy], [(0, c.params), (0, other)]) == -1
+
+
+def test_ensemble_step_refuses_a_single_model_context(lib):
+    c = synth.config1(n=4)
+    rc, h = _create(c.mesh, c.bathy, c.params)
+    assert rc == 0
+    assert lib.dgswem_ensemble_step(h, 1) == -1
+    lib.dgswem_destroy(h)
