@@ -159,7 +159,7 @@ def kernel_timed_steps(steps):
     return (steps + KERNEL_TIMING_EVERY - 1) // KERNEL_TIMING_EVERY
 
 
-def time_steps(model, steps, warmup, stream, flush, per_kernel=False):
+def time_steps(model, steps, warmup, stream, flush, per_kernel=False, dist=None):
     """Per-step CUDA-event timing on the library's stream, L2 flushed between steps.
 
     With per_kernel, every KERNEL_TIMING_EVERY-th timed step replays the graph variant with
@@ -174,6 +174,10 @@ def time_steps(model, steps, warmup, stream, flush, per_kernel=False):
     if per_kernel:  # capture both graphs before the timed region
         model.set_kernel_timing(True)
         model.set_kernel_timing(False)
+    torch.cuda.synchronize()
+    if dist:  # every rank starts its timed steps together
+        dist.barrier()
+    torch.cuda.synchronize()
     torch.cuda.profiler.start()  # an ncu run with --profile-from-start off sees only these steps
     for i in range(steps):
         timed = per_kernel and i % KERNEL_TIMING_EVERY == 0
@@ -189,17 +193,20 @@ def time_steps(model, steps, warmup, stream, flush, per_kernel=False):
             for name, ms in model.kernel_times():
                 kt.setdefault(name, []).append(ms)
     stream.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     torch.cuda.profiler.stop()
     model.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
     return ms, kt
 
 
-def run_form(case, steps, warmup, stream, flush, per_kernel=True, **kw):
+def run_form(case, steps, warmup, stream, flush, per_kernel=True, dist=None, **kw):
     m = make_model(case, stream, **kw)
     if per_kernel:
         m.set_kernel_timing(True)
-    ms, kt = time_steps(m, steps, warmup, stream, flush, per_kernel)
+    ms, kt = time_steps(m, steps, warmup, stream, flush, per_kernel, dist)
     kps, variant, block = m.graph_info()
     return m, ms, kt, (kps, variant, block)
 
@@ -362,15 +369,9 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     case = synth.config2()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        model, ms, kt, (kps, variant, block) = run_form(case, args.steps, args.warmup, stream, flush)
-    torch.cuda.synchronize()
+        model, ms, kt, (kps, variant, block) = run_form(case, args.steps, args.warmup, stream, flush, dist=dist)
     total_s, units = aggregate(sum(ms) * 1e-3, case.mesh.n_elems * 2 * args.steps, dist, "cuda")
-    if dist:
-        dist.barrier()
     value = units / total_s
     if rank != 0:
         if dist:
