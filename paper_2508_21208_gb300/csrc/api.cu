@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -150,6 +151,28 @@ static std::vector<char> typed(const std::vector<double> &v, bool mixed) {
   return out;
 }
 
+// double -> float as the kernels convert (round to nearest even; magnitudes below float's normal
+// range give a signed zero), so that a value rounded here equals the one a kernel would compute.
+static float device_float(double x) {
+  if (std::fabs(x) < (double)FLT_MIN) return std::signbit(x) ? -0.0f : 0.0f;
+  return (float)x;
+}
+
+// The float form's per-element vertex data: h_b, x and y at the three vertices ([9][ne]).
+static std::vector<char> element_floats(const HostMesh &H) {
+  const size_t ne = H.ne, nn = H.nn;
+  std::vector<char> out(9 * ne * sizeof(float));
+  float *f = reinterpret_cast<float *>(out.data());
+  for (size_t e = 0; e < ne; ++e)
+    for (int a = 0; a < 3; ++a) {
+      const size_t n = (size_t)H.vnode[a * ne + e];
+      f[a * ne + e] = device_float(H.hbv[a * ne + e]);
+      f[(3 + a) * ne + e] = device_float(H.nodexy[n]);
+      f[(6 + a) * ne + e] = device_float(H.nodexy[nn + n]);
+    }
+  return out;
+}
+
 // ------------------------------------------------------------------ workspace layout
 void carve_mesh(Carver &k, const HostMesh &H, int p, bool mixed, DevMesh &m, int **perm, int **iperm) {
   const int ne = H.ne, nn = H.nn, nint = H.nint;
@@ -175,6 +198,7 @@ void carve_mesh(Carver &k, const HostMesh &H, int p, bool mixed, DevMesh &m, int
   m.hbq = mixed ? nullptr : k.take<char>(tsz * nqa_of(p) * ne);
   m.edhbq = mixed ? nullptr : k.take<char>(tsz * nqe_of(p) * nint);
   m.nodexy = k.take<double>(2 * (size_t)nn);
+  m.elf = mixed ? k.take<float>(9 * (size_t)ne) : nullptr;
   *perm = k.take<int>(ne);
   *iperm = k.take<int>(ne);
 }
@@ -445,6 +469,10 @@ int upload_mesh(dgswem_ctx *c, const HostMesh &H, const DevMesh &m, int *perm, i
   if (m.hbq) r |= put(m.hbq, c->host_keep[base + 3].data(), c->host_keep[base + 3].size());
   if (m.edhbq) r |= put(m.edhbq, c->host_keep[base + 4].data(), c->host_keep[base + 4].size());
   r |= put(m.nodexy, H.nodexy.data(), H.nodexy.size() * sizeof(double));
+  if (m.elf) {
+    c->host_keep.push_back(element_floats(H));
+    r |= put(m.elf, c->host_keep.back().data(), c->host_keep.back().size());
+  }
   r |= put(perm, H.perm.data(), H.perm.size() * sizeof(int));
   r |= put(iperm, H.iperm.data(), H.iperm.size() * sizeof(int));
   return r ? c->sticky : 0;

@@ -48,7 +48,7 @@ struct EnsembleState {
   std::vector<int> h_etile, h_ntile;
   std::vector<MemberDev> h_mem;
   bool persistent = true;
-  int block = 128, grid = 0, fault = 0, any_limwd = 0;
+  int block = 128, grid = 0, fault = 0, any_limwd = 0, any_inline = 0;
   unsigned long long timeout_ns = 1000000000ull;  // 1 s per grid-barrier wait
   std::vector<TuneEntry> tune;
 };
@@ -100,6 +100,7 @@ static void build_tiles(dgswem_ctx *c, int block) {
   E.h_ntile.clear();
   E.h_mem.assign(E.mem.size(), MemberDev{});
   E.any_limwd = 0;
+  E.any_inline = 0;
   for (size_t i = 0; i < E.mem.size(); ++i) {
     EnsMember &mb = E.mem[i];
     const EnsMesh &M = E.meshes[mb.mesh];
@@ -119,6 +120,7 @@ static void build_tiles(dgswem_ctx *c, int block) {
     const int nt = (M.hm.ne + block - 1) / block;
     for (int t = 0; t < nt; ++t) E.h_etile.push_back((int)i);
     E.any_limwd |= (mb.ph.limiter || mb.ph.wetdry) ? 1 : 0;
+    E.any_inline |= (mb.ph.hurricane && c->mixed) ? 1 : 0;
   }
   for (size_t i = 0; i < E.mem.size(); ++i) {
     EnsMember &mb = E.mem[i];
@@ -179,7 +181,7 @@ static int grid_for(dgswem_ctx *c, int block) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = ensemble_blocks_per_sm(c->mixed, c->P, block);
+  const int per_sm = ensemble_blocks_per_sm(c->mixed, c->P, block, c->ens->any_inline != 0);
   return std::min(c->ens->n_etile, per_sm * sms);
 }
 
@@ -204,6 +206,7 @@ void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names) {
   a.err = c->err;
   a.fault = E.fault;
   a.any_limwd = E.any_limwd;
+  a.any_inline = E.any_inline;
   a.timeout_ns = E.timeout_ns;
   if (names) {
     cudaEventRecordWithFlags(c->ev[0], c->st, cudaEventRecordExternal);

@@ -121,6 +121,8 @@ struct DevMesh {
   const void *hbq;         // T [NQA][ne]: h_b at the area quadrature points
   const void *edhbq;       // T [NQE][nint]: h_b at the interior edges' Gauss points
   const double *nodexy;    // [2][nn]
+  const float *elf;        // float form: [9][ne] vertex h_b (3), vertex x (3), vertex y (3), rounded
+                           // once on the host like the kernels' double -> float conversion
 };
 
 
@@ -190,6 +192,7 @@ struct EnsArgs {
   int *err;
   int fault;               // test hook: the last block never arrives at a barrier
   int any_limwd;
+  int any_inline;          // some member evaluates the vortex inline (float form): tile_smem_bytes(, true)
   unsigned long long timeout_ns;
 };
 
@@ -246,7 +249,7 @@ struct LaunchCfg {
   void prepare_tile_##SUF();                                                                      \
   cudaError_t launch_ensemble_##SUF(int p, bool persistent, const EnsArgs &a, int block, int grid, \
                                     cudaStream_t s);                                             \
-  int ensemble_blocks_per_sm_##SUF(int p, int block);
+  int ensemble_blocks_per_sm_##SUF(int p, int block, bool ef);
 DG_DECLARE_LAUNCHERS(f64)
 DG_DECLARE_LAUNCHERS(f32)
 #undef DG_DECLARE_LAUNCHERS
@@ -280,8 +283,8 @@ inline cudaError_t launch_ensemble(bool mixed, int p, bool persistent, const Ens
   return mixed ? launch_ensemble_f32(p, persistent, a, block, grid, s)
                : launch_ensemble_f64(p, persistent, a, block, grid, s);
 }
-inline int ensemble_blocks_per_sm(bool mixed, int p, int block) {
-  return mixed ? ensemble_blocks_per_sm_f32(p, block) : ensemble_blocks_per_sm_f64(p, block);
+inline int ensemble_blocks_per_sm(bool mixed, int p, int block, bool ef) {
+  return mixed ? ensemble_blocks_per_sm_f32(p, block, ef) : ensemble_blocks_per_sm_f64(p, block, ef);
 }
 void upload_common_tables(const Tab<double> td[2]);
 

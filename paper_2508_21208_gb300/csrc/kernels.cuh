@@ -635,10 +635,14 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
 }
 
 // Inverse mass matrix, closed-form linear sources and the RK stage; writes u^(s+1) and the means.
+// ctr: the storm centre at the stage time (once per block), or null; vxy: the element's vertex
+// coordinates already in T (x0, x1, x2 at vxy[0], vxy[vs], vxy[2 vs], then y), or null to read the
+// nodes.
 template <int P, typename T>
 __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s, const Phys &ph,
                                             const int write_rhs, const int e, const ElemCtx<P, T> &c,
-                                            T r[3][nd_of(P)], const double *ctr = nullptr) {
+                                            T r[3][nd_of(P)], const double *ctr = nullptr,
+                                            const T *vxy = nullptr, const int vs = 0) {
   constexpr int ND = nd_of(P);
   const Tab<T> &tb = ctab<T>(P);
   const int ne = m.ne;
@@ -659,7 +663,6 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
     }
     if (s.frc || s.frc_inline) {
       const int nn = m.nn;
-      const int n0 = m.vnode[e], n1 = m.vnode[ne + e], n2 = m.vnode[2 * (size_t)ne + e];
       T t0, t1, t2, u0, u1, u2, p0, p1, p2;
       if (s.frc_inline) {
         // the centre once per element (or per block: ctr); vertex offsets in T (O(1e5) m
@@ -672,10 +675,26 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
           storm_center(ph, stage_time(s.clk, s.tau, s.tide_t), cxd, cyd);
         }
         const T cx = from_d<T>(cxd), cy = from_d<T>(cyd);
-        vortex_at<T>(ph, from_d<T>(m.nodexy[n0]) - cx, from_d<T>(m.nodexy[nn + n0]) - cy, t0, u0, p0);
-        vortex_at<T>(ph, from_d<T>(m.nodexy[n1]) - cx, from_d<T>(m.nodexy[nn + n1]) - cy, t1, u1, p1);
-        vortex_at<T>(ph, from_d<T>(m.nodexy[n2]) - cx, from_d<T>(m.nodexy[nn + n2]) - cy, t2, u2, p2);
+        T x[3], y[3];
+        if (vxy) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            x[a] = vxy[a * vs];
+            y[a] = vxy[(3 + a) * vs];
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const int n = m.vnode[(size_t)a * ne + e];
+            x[a] = from_d<T>(m.nodexy[n]);
+            y[a] = from_d<T>(m.nodexy[nn + n]);
+          }
+        }
+        vortex_at<T>(ph, x[0] - cx, y[0] - cy, t0, u0, p0);
+        vortex_at<T>(ph, x[1] - cx, y[1] - cy, t1, u1, p1);
+        vortex_at<T>(ph, x[2] - cx, y[2] - cy, t2, u2, p2);
       } else {
+        const int n0 = m.vnode[e], n1 = m.vnode[ne + e], n2 = m.vnode[2 * (size_t)ne + e];
         const T *F = (const T *)s.frc;
         t0 = F[n0]; t1 = F[n1]; t2 = F[n2];
         u0 = F[nn + n0]; u1 = F[nn + n1]; u2 = F[nn + n2];
@@ -869,10 +888,25 @@ __global__ void __launch_bounds__(256)
 // flux of each (element, local edge, Gauss point) in shared memory; after one barrier each thread
 // finishes its element (area integrals, gather in the fixed local-edge order, inverse mass, RK).
 // Shared memory: double state [3*ND][tile], float/double flux slots [3][NQE][3][tile], flags.
+// ef: the float form with the inline vortex adds TILE_EF rows of the element phase's inputs (J^-1,
+// det J, vertex h_b, vertex x and y), copied asynchronously at the start of the tile.
+constexpr int TILE_EF = 14;
 template <int P, typename T>
-__host__ __device__ constexpr size_t tile_smem_bytes(int tile) {
-  return sizeof(T) * 3 * nd_of(P) * tile + sizeof(T) * 9 * nqe_of(P) * tile + tile;
+__host__ __device__ constexpr size_t tile_smem_bytes(int tile, bool ef = false) {
+  return sizeof(T) * 3 * nd_of(P) * tile + sizeof(T) * 9 * nqe_of(P) * tile +
+         (ef && sizeof(T) == sizeof(float) ? sizeof(float) * TILE_EF * tile : 0) + tile;
 }
+
+// Asynchronous 4-byte global -> shared copy (cp.async, cached in L1) and its completion.
+__device__ __forceinline__ void cp_async4(void *dst_shared, const void *src_global) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+  asm volatile(
+      "{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %1;\n\tcp.async.ca.shared.global [%0], [g], 4;\n\t}" ::"r"(d),
+      "l"(src_global)
+      : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Modes of element e: from the tile's shared-memory copy (already in T) or, for a neighbour in
 // another tile, from global memory.
@@ -985,13 +1019,28 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
                                           const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
   constexpr int ND = nd_of(P), NQE = nqe_of(P);
   const int B = tl.tile, ne = m.ne;
+  // float form with the inline vortex: the element phase's inputs are prefetched to shared memory
+  // (the launch sized the dynamic shared memory with tile_smem_bytes(tile, true))
+  const bool ef = sizeof(T) == sizeof(float) && s.frc_inline;
   T *s_ud = reinterpret_cast<T *>(smem_raw);
   T *s_slot = s_ud + (size_t)3 * ND * B;
-  uint8_t *s_wd = reinterpret_cast<uint8_t *>(s_slot + (size_t)9 * NQE * B);
+  float *s_ef = reinterpret_cast<float *>(s_slot + (size_t)9 * NQE * B);
+  uint8_t *s_wd = reinterpret_cast<uint8_t *>(s_ef + (ef ? (size_t)TILE_EF * B : 0));
   const int e0 = tile * B, i = threadIdx.x;
   const int nloc = min(B, ne - e0);
   __shared__ double s_ctr[2];  // storm centre at the stage time, once per block (inline vortex)
   if (s.frc_inline && i == 0) storm_center(ph, stage_time(s.clk, s.tau, s.tide_t), s_ctr[0], s_ctr[1]);
+  if (ef) {
+    // in flight while the states are staged and the edges computed
+    if (i < nloc) {
+      const float *geo = (const float *)m.geo;
+#pragma unroll
+      for (int r = 0; r < 5; ++r) cp_async4(&s_ef[r * B + i], &geo[(size_t)(GEO_RX + r) * ne + e0 + i]);
+#pragma unroll
+      for (int r = 0; r < 9; ++r) cp_async4(&s_ef[(5 + r) * B + i], &m.elf[(size_t)r * ne + e0 + i]);
+    }
+    cp_async_commit();
+  }
   if (i < nloc) {
 #pragma unroll
     for (int r = 0; r < 3 * ND; ++r) s_ud[r * B + i] = from_d<T>(__ldg(&s.uin[(size_t)r * ne + e0 + i]));
@@ -1000,11 +1049,25 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
   __syncthreads();
   const int beg = tl.start[tile], end = tl.start[tile + 1];
   for (int x = beg + i; x < end; x += B) tile_edge<P, T>(m, tl, s, ph, x, e0, s_ud, s_slot, s_wd, s_phe);
+  if (ef) cp_async_wait_all();  // each thread reads only the rows it copied
   __syncthreads();
   if (i < nloc) {
     const int e = e0 + i;
     ElemCtx<P, T> c;
-    elem_load_geom<P, T>(m, e, c);
+    if (ef) {
+      c.rx = s_ef[i];
+      c.ry = s_ef[B + i];
+      c.sx = s_ef[2 * B + i];
+      c.sy = s_ef[3 * B + i];
+      c.dJ = s_ef[4 * B + i];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        c.hb[a] = s_ef[(5 + a) * B + i];
+        c.hbd[a] = 0.0;  // the double vertex depths serve the untiled variants only
+      }
+    } else {
+      elem_load_geom<P, T>(m, e, c);
+    }
 #pragma unroll
     for (int v = 0; v < 3; ++v)
 #pragma unroll
@@ -1022,7 +1085,7 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
 #pragma unroll
           for (int k = 1; k < ND; ++k) r[v][k] -= f * s_phe[l][q][k];
         }
-    elem_finish<P, T>(m, s, ph, write_rhs, e, c, r, s_ctr);
+    elem_finish<P, T>(m, s, ph, write_rhs, e, c, r, s_ctr, ef ? (const T *)&s_ef[8 * B + i] : nullptr, B);
   }
   __syncthreads();  // the shared-memory tile is reused by the block's next tile
 }
@@ -1471,7 +1534,7 @@ cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int bloc
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
     cfg.stream = s;
-    cfg.dynamicSmemBytes = p == 1 ? tile_smem_bytes<1, T>(block) : tile_smem_bytes<2, T>(block);
+    cfg.dynamicSmemBytes = p == 1 ? tile_smem_bytes<1, T>(block, a.any_inline) : tile_smem_bytes<2, T>(block, a.any_inline);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
@@ -1480,7 +1543,7 @@ cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int bloc
     return p == 1 ? cudaLaunchKernelEx(&cfg, k_ens_persistent<1, T>, a)
                   : cudaLaunchKernelEx(&cfg, k_ens_persistent<2, T>, a);
   }
-  const size_t sm = p == 1 ? tile_smem_bytes<1, T>(block) : tile_smem_bytes<2, T>(block);
+  const size_t sm = p == 1 ? tile_smem_bytes<1, T>(block, a.any_inline) : tile_smem_bytes<2, T>(block, a.any_inline);
   for (int stage = 0; stage < a.nstages; ++stage) {
     if (a.n_ntile > 0) {
       if (p == 1) k_ens_phase<1, T><<<a.n_ntile, block, sm, s>>>(a, 0, stage);
@@ -1497,12 +1560,12 @@ cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int bloc
 }
 
 template <typename T>
-int ensemble_blocks_per_sm_t(int p, int block) {
+int ensemble_blocks_per_sm_t(int p, int block, bool ef) {
   int n = 0;
   if (p == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<1, T>, block, tile_smem_bytes<1, T>(block));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<1, T>, block, tile_smem_bytes<1, T>(block, ef));
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<2, T>, block, tile_smem_bytes<2, T>(block));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_persistent<2, T>, block, tile_smem_bytes<2, T>(block, ef));
   return n;
 }
 
@@ -1558,7 +1621,7 @@ void launch_tile_t(int p, bool wide, bool write_rhs, const DevMesh &m, const Dev
                    const Phys &ph, const LaunchCfg &c) {
   const int wr = write_rhs ? 1 : 0;
   if (p == 1) {
-    const size_t sm = tile_smem_bytes<1, T>(tl.tile);
+    const size_t sm = tile_smem_bytes<1, T>(tl.tile, s.frc_inline != 0);
     if constexpr (sizeof(T) == sizeof(float)) {
       if (wide) {
         k_tile<1, T, true><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
@@ -1567,7 +1630,7 @@ void launch_tile_t(int p, bool wide, bool write_rhs, const DevMesh &m, const Dev
     }
     k_tile<1, T, false><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
   } else {
-    const size_t sm = tile_smem_bytes<2, T>(tl.tile);
+    const size_t sm = tile_smem_bytes<2, T>(tl.tile, s.frc_inline != 0);
     k_tile<2, T, false><<<tl.ntiles, tl.tile, sm, c.stream>>>(m, tl, s, ph, wr);
   }
 }
@@ -1575,17 +1638,17 @@ void launch_tile_t(int p, bool wide, bool write_rhs, const DevMesh &m, const Dev
 template <typename T>
 void prepare_tile_t() {
   // allow the largest tile's dynamic shared memory (p = 2, 256 elements)
-  cudaFuncSetAttribute(k_tile<1, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256));
+  cudaFuncSetAttribute(k_tile<1, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256, true));
   if constexpr (sizeof(T) == sizeof(float))
     cudaFuncSetAttribute(k_tile<1, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tile_smem_bytes<1, T>(256));
-  cudaFuncSetAttribute(k_tile<2, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256));
+                         (int)tile_smem_bytes<1, T>(256, true));
+  cudaFuncSetAttribute(k_tile<2, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256, true));
   cudaFuncSetAttribute(k_ens_persistent<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tile_smem_bytes<1, T>(256));
+                       (int)tile_smem_bytes<1, T>(256, true));
   cudaFuncSetAttribute(k_ens_persistent<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tile_smem_bytes<2, T>(256));
-  cudaFuncSetAttribute(k_ens_phase<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256));
-  cudaFuncSetAttribute(k_ens_phase<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256));
+                       (int)tile_smem_bytes<2, T>(256, true));
+  cudaFuncSetAttribute(k_ens_phase<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<1, T>(256, true));
+  cudaFuncSetAttribute(k_ens_phase<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256, true));
 }
 
 template <typename T>

@@ -24,7 +24,7 @@ void launch_limwd_f32(int p, bool do_lim, int do_wd, const DevMesh &m, double *u
 cudaError_t launch_ensemble_f32(int p, bool persistent, const EnsArgs &a, int block, int grid, cudaStream_t s) {
   return launch_ensemble_t<float>(p, persistent, a, block, grid, s);
 }
-int ensemble_blocks_per_sm_f32(int p, int block) { return ensemble_blocks_per_sm_t<float>(p, block); }
+int ensemble_blocks_per_sm_f32(int p, int block, bool ef) { return ensemble_blocks_per_sm_t<float>(p, block, ef); }
 
 void launch_tile_f32(int p, bool wide, bool write_rhs, const DevMesh &m, const DevTiles &tl, const StageArgs &s,
                      const Phys &ph, const LaunchCfg &c) {
