@@ -213,7 +213,7 @@ static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
   c->U0 = k.take<double>(nu);
   c->U1 = k.take<double>(nu);
   c->U2 = c->nst >= 3 ? k.take<double>(nu) : nullptr;
-  c->mean = k.take<double>(3 * (size_t)ne);
+  c->mean = k.take<char>(tsz * 3 * ne);
   c->wd = k.take<uint8_t>(ne);
   c->wd_stage = k.take<uint8_t>(ne);
   c->eflux = k.take<char>(tsz * 3 * NQE * nint);
@@ -818,7 +818,7 @@ int dgswem_apply_limiter(dgswem_ctx *c) {
   if (c->ensemble) return ctx_fail(c, DGSWEM_EINVAL, "not available for an ensemble");
   if (c->sticky) return c->sticky;
   if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
-  launch_copy_means(c->P, c->hm.ne, c->U0, c->mean, c->st);
+  launch_copy_means(c->mixed, c->P, c->hm.ne, c->U0, c->mean, c->st);
   launch_limwd(c->mixed, c->P, true, 0, c->dm, c->U0, c->mean, c->wd, c->ph, c->err, LaunchCfg{c->block, c->st});
   if (int r = ctx_cuda(c, cudaGetLastError(), "limiter")) return r;
   return read_error_word(c);

@@ -50,8 +50,8 @@ struct dgswem_ctx {
   dg::TileEdges htiles;
   dg::Phys ph{};
   int *d_perm = nullptr, *d_iperm = nullptr;
-  double *U0 = nullptr, *U1 = nullptr, *U2 = nullptr, *mean = nullptr, *partial = nullptr, *result = nullptr,
-         *staging = nullptr;
+  double *U0 = nullptr, *U1 = nullptr, *U2 = nullptr, *partial = nullptr, *result = nullptr, *staging = nullptr;
+  void *mean = nullptr;  // T [3][ne] element means for the limiter
   uint8_t *wd = nullptr, *wd_stage = nullptr, *emode = nullptr;
   void *eflux = nullptr, *frc = nullptr;
   long long *step = nullptr;

@@ -34,16 +34,6 @@ void launch_init_nodal(int p, const DevMesh &m, const double *nodal, double *u, 
   k_init_nodal<<<nblk(m.ne, 256), 256, 0, s>>>(nd_of(p), m.ne, m.nn, m.vnode, nodal, u);
 }
 
-__global__ void k_copy_means(int nd, int ne, const double *u, double *mean) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
-  for (int v = 0; v < 3; ++v) mean[(size_t)v * ne + e] = u[(size_t)v * nd * ne + e];
-}
-
-void launch_copy_means(int p, int ne, const double *u, double *mean, cudaStream_t s) {
-  k_copy_means<<<nblk(ne, 256), 256, 0, s>>>(nd_of(p), ne, u, mean);
-}
-
 // dt = cfl * 3/(2p+1) * min_e r_e / lambda_e with lambda_e = max over vertices of
 // |u| + sqrt(g max(H, h0)).  Positive doubles order like their bit patterns, so the minimum is
 // an exact, order-independent atomicMin on the 64-bit pattern.

@@ -22,7 +22,8 @@ struct EnsMember {
   int init_kind = 0;
   std::vector<double> init_modal, init_nodal;
   double t0 = 0.0, dt = 0.0;
-  double *U0 = nullptr, *U1 = nullptr, *U2 = nullptr, *mean = nullptr;
+  double *U0 = nullptr, *U1 = nullptr, *U2 = nullptr;
+  void *mean = nullptr;  // T [3][ne]
   uint8_t *wd = nullptr;
   void *frc = nullptr;
 };
@@ -76,7 +77,7 @@ static void ens_layout(dgswem_ctx *c, char *base, size_t *bytes) {
     mb.U0 = k.take<double>(nu);
     mb.U1 = k.take<double>(nu);
     mb.U2 = c->nst >= 3 ? k.take<double>(nu) : nullptr;
-    mb.mean = k.take<double>(3 * (size_t)H.ne);
+    mb.mean = k.take<char>(tsz * 3 * (size_t)H.ne);
     mb.wd = k.take<uint8_t>(H.ne);
     mb.frc = k.take<char>(tsz * 3 * H.nn);
     stage = std::max(stage, std::max(nu, 3 * (size_t)H.nn));

@@ -141,7 +141,7 @@ struct StageArgs {
   const double *uin;       // u^(s): [3][ND][ne]
   const double *un;        // u^n (second stage only)
   double *uout;            // u^(s+1)
-  double *mean;            // [3][ne] element means of u^(s+1), read by the limiter
+  void *mean;              // T [3][ne] element means of u^(s+1), read by the limiter
   const uint8_t *wd;       // wet/dry flags
   void *eflux;             // T [3][NQE][nint] weighted interior-edge fluxes (split variant)
   uint8_t *emode;          // [nint] 1 = the edge flux in eflux applies, 0 = both sides see a wall
@@ -172,7 +172,8 @@ struct MemberDev {
   DevMesh m;               // the member's mesh statics (shared with members on the same mesh)
   DevTiles tl;             // the mesh's tile edge lists for the ensemble's tile size
   Phys ph;
-  double *U0, *U1, *U2, *mean;  // its own state (U2 only for three or more stages)
+  double *U0, *U1, *U2;    // its own state (U2 only for three or more stages)
+  void *mean;              // T [3][ne] element means for the limiter
   uint8_t *wd;
   void *frc;               // T [3][nn]
   double t0, dt;           // stage time = t0 + (step + stage) * dt (its own dt)
@@ -242,14 +243,15 @@ struct LaunchCfg {
   void launch_element_##SUF(int p, bool split, bool write_rhs, const DevMesh &m,                 \
                             const StageArgs &s, const Phys &ph, const LaunchCfg &c);             \
   void launch_limwd_##SUF(int p, bool do_lim, int do_wd, const DevMesh &m, double *u,            \
-                          const double *mean, uint8_t *wd, const Phys &ph, int *err,             \
+                          const void *mean, uint8_t *wd, const Phys &ph, int *err,               \
                           const LaunchCfg &c);                                                   \
   void launch_tile_##SUF(int p, bool wide, bool write_rhs, const DevMesh &m, const DevTiles &tl,   \
                          const StageArgs &s, const Phys &ph, const LaunchCfg &c);                 \
   void prepare_tile_##SUF();                                                                      \
   cudaError_t launch_ensemble_##SUF(int p, bool persistent, const EnsArgs &a, int block, int grid, \
                                     cudaStream_t s);                                             \
-  int ensemble_blocks_per_sm_##SUF(int p, int block, bool ef);
+  int ensemble_blocks_per_sm_##SUF(int p, int block, bool ef);                                  \
+  void launch_copy_means_##SUF(int p, int ne, const double *u, void *mean, cudaStream_t s);
 DG_DECLARE_LAUNCHERS(f64)
 DG_DECLARE_LAUNCHERS(f32)
 #undef DG_DECLARE_LAUNCHERS
@@ -269,7 +271,7 @@ inline void launch_element(bool mixed, int p, bool split, bool write_rhs, const 
         : launch_element_f64(p, split, write_rhs, m, s, ph, c);
 }
 inline void launch_limwd(bool mixed, int p, bool do_lim, int do_wd, const DevMesh &m, double *u,
-                         const double *mean, uint8_t *wd, const Phys &ph, int *err,
+                         const void *mean, uint8_t *wd, const Phys &ph, int *err,
                          const LaunchCfg &c) {
   mixed ? launch_limwd_f32(p, do_lim, do_wd, m, u, mean, wd, ph, err, c)
         : launch_limwd_f64(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
@@ -283,6 +285,10 @@ inline cudaError_t launch_ensemble(bool mixed, int p, bool persistent, const Ens
   return mixed ? launch_ensemble_f32(p, persistent, a, block, grid, s)
                : launch_ensemble_f64(p, persistent, a, block, grid, s);
 }
+// element means of u into the limiter's mean array (T [3][ne])
+inline void launch_copy_means(bool mixed, int p, int ne, const double *u, void *mean, cudaStream_t s) {
+  mixed ? launch_copy_means_f32(p, ne, u, mean, s) : launch_copy_means_f64(p, ne, u, mean, s);
+}
 inline int ensemble_blocks_per_sm(bool mixed, int p, int block, bool ef) {
   return mixed ? ensemble_blocks_per_sm_f32(p, block, ef) : ensemble_blocks_per_sm_f64(p, block, ef);
 }
@@ -290,7 +296,6 @@ void upload_common_tables(const Tab<double> td[2]);
 
 // precision-independent kernels (common_kernels.cu)
 void launch_init_nodal(int p, const DevMesh &m, const double *nodal, double *u, cudaStream_t s);
-void launch_copy_means(int p, int ne, const double *u, double *mean, cudaStream_t s);
 void launch_dt(int p, const DevMesh &m, const double *u, const Phys &ph, unsigned long long *best,
                cudaStream_t s);
 void launch_mass(int p, const DevMesh &m, const double *u, double *partial, double *result,

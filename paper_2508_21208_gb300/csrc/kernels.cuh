@@ -756,7 +756,7 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
       }
       bad |= !finite_bits(out);
       s.uout[ix] = out;
-      if (k == 0 && s.mean) s.mean[(size_t)v * ne + e] = out;
+      if (k == 0 && s.mean) static_cast<T *>(s.mean)[(size_t)v * ne + e] = from_d<T>(out);
     }
   }
   if (bad) atomicOr(s.err, ERR_NONFINITE);
@@ -1191,7 +1191,7 @@ __device__ __noinline__ void limiter_rebuild(const T d0, const T d1, const T d2,
 }
 
 template <int P, typename T>
-__device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const double *mean, uint8_t *wd,
+__device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const T *mean, uint8_t *wd,
                                            const Phys &ph, int *err, int do_lim, int do_wd, const int e) {
   constexpr int ND = nd_of(P);
   const int ne = m.ne;
@@ -1209,9 +1209,9 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
       const double d0 = u[(size_t)(v * ND) * ne + e];
       const double d1 = u[(size_t)(v * ND + 1) * ne + e];
       const double d2 = u[(size_t)(v * ND + 2) * ne + e];
-      double db3[3];
+      T db3[3];  // neighbour means (stored in T: the float form rounds them once, when written)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) db3[j] = nb[j] >= 0 ? mean[(size_t)v * ne + nb[j]] : d0;
+      for (int j = 0; j < 3; ++j) db3[j] = nb[j] >= 0 ? mean[(size_t)v * ne + nb[j]] : from_d<T>(d0);
       if constexpr (sizeof(T) == sizeof(double)) {
         // Filtered predicate (after Shewchuk's floating-point filters): a float evaluation with an
         // error margin well above its rounding proves, when it can, that minmod returns the midpoint
@@ -1246,7 +1246,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
       const T u2 = from_d<T>(d2);
       T dd[3];  // neighbour mean minus own mean
 #pragma unroll
-      for (int j = 0; j < 3; ++j) dd[j] = from_d<T>(db3[j]) - u0;
+      for (int j = 0; j < 3; ++j) dd[j] = db3[j] - u0;
       // midpoint deviations of the linear part; in double from the linear Dubiner modes at the
       // edge midpoints, (1/2, 1/2), (-1/2, 1/2) and (0, -1) (Eq. dubiner): the same values as the
       // table products (halving is exact), from two additions
@@ -1286,14 +1286,22 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
   if (do_wd) {  // 1: apply the operator, 2: classify only (flags from the current state)
     const bool write = do_wd == 1;
     const double h0 = ph.h0;
-    const double hbv[3] = {m.hbv[e], m.hbv[ne + e], m.hbv[2 * (size_t)ne + e]};
     const double z0 = u[e], z1 = u[(size_t)ne + e], z2 = u[2 * (size_t)ne + e];
     {
       // Filtered predicate: a float evaluation decides the clearly wet elements (every vertex depth
       // exceeds h0 by far more than the float rounding of its terms), for which the double test
       // below would change nothing; only the rest are tested in double.
       const float fz0 = d2f(z0), fz1 = d2f(z1), fz2 = d2f(z2);
-      const float fh0 = d2f(hbv[0]), fh1 = d2f(hbv[1]), fh2 = d2f(hbv[2]);
+      float fh0, fh1, fh2;
+      if constexpr (sizeof(T) == sizeof(float)) {  // the float form's copy: the same rounded values
+        fh0 = m.elf[e];
+        fh1 = m.elf[ne + e];
+        fh2 = m.elf[2 * (size_t)ne + e];
+      } else {
+        fh0 = d2f(m.hbv[e]);
+        fh1 = d2f(m.hbv[ne + e]);
+        fh2 = d2f(m.hbv[2 * (size_t)ne + e]);
+      }
       const float mag = fabsf(fz0) + fabsf(fz1) + 2.f * fabsf(fz2) + fmaxf(fabsf(fh0), fmaxf(fabsf(fh1), fabsf(fh2)));
       const float margin = 1e-6f * mag + 1e-6f;
       const float lo = fminf(fz0 - fz1 - fz2 + fh0, fminf(fz0 + fz1 - fz2 + fh1, fz0 + 2.f * fz2 + fh2));
@@ -1302,6 +1310,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
         return;
       }
     }
+    const double hbv[3] = {m.hbv[e], m.hbv[ne + e], m.hbv[2 * (size_t)ne + e]};
     // zeta at the reference vertices (-1,-1), (1,-1), (-1,1): psi_10 = (-1, 1, 0), psi_01 = (-1, -1, 2)
     double H[3] = {z0 - z1 - z2 + hbv[0], z0 + z1 - z2 + hbv[1], z0 + 2.0 * z2 + hbv[2]};
     const double Hs = H[0] + H[1] + H[2];  // 3 x mean depth
@@ -1356,7 +1365,7 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const do
 }
 
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_limwd(const DevMesh m, double *u, const double *mean,
+__global__ void __launch_bounds__(256) k_limwd(const DevMesh m, double *u, const T *mean,
                                                uint8_t *wd, const Phys ph, int *err, int do_lim,
                                                int do_wd) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1482,7 +1491,8 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
       } else if (sd->ph.limiter || sd->ph.wetdry) {
         double *in, *out;
         stage_buffers(stage, a.nstages, sd->U0, sd->U1, sd->U2, in, out);
-        limwd_body<P, T>(sd->m, out, sd->mean, sd->wd, sd->ph, a.err, sd->ph.limiter, sd->ph.wetdry, e);
+        limwd_body<P, T>(sd->m, out, static_cast<const T *>(sd->mean), sd->wd, sd->ph, a.err, sd->ph.limiter,
+                         sd->ph.wetdry, e);
       }
     }
   }
@@ -1651,9 +1661,22 @@ void prepare_tile_t() {
   cudaFuncSetAttribute(k_ens_phase<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<2, T>(256, true));
 }
 
+// Element means of u into the limiter's mean array, rounded to T as the element kernels round them.
 template <typename T>
-void launch_limwd_t(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean, uint8_t *wd,
+__global__ void k_copy_means(int nd, int ne, const double *u, T *mean) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  for (int v = 0; v < 3; ++v) mean[(size_t)v * ne + e] = from_d<T>(u[(size_t)v * nd * ne + e]);
+}
+template <typename T>
+void launch_copy_means_t(int p, int ne, const double *u, void *mean, cudaStream_t s) {
+  k_copy_means<T><<<nblocks(ne, 256), 256, 0, s>>>(nd_of(p), ne, u, static_cast<T *>(mean));
+}
+
+template <typename T>
+void launch_limwd_t(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const void *mean_v, uint8_t *wd,
                     const Phys &ph, int *err, const LaunchCfg &c) {
+  const T *mean = static_cast<const T *>(mean_v);
   const int nb = nblocks(m.ne, c.block);
   if (p == 1)
     k_limwd<1, T><<<nb, c.block, 0, c.stream>>>(m, u, mean, wd, ph, err, do_lim, do_wd);

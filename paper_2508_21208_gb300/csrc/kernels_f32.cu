@@ -16,7 +16,7 @@ void launch_element_f32(int p, bool split, bool write_rhs, const DevMesh &m, con
                         const Phys &ph, const LaunchCfg &c) {
   launch_element_t<float>(p, split, write_rhs, m, s, ph, c);
 }
-void launch_limwd_f32(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean,
+void launch_limwd_f32(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const void *mean,
                       uint8_t *wd, const Phys &ph, int *err, const LaunchCfg &c) {
   launch_limwd_t<float>(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
 }
@@ -31,5 +31,8 @@ void launch_tile_f32(int p, bool wide, bool write_rhs, const DevMesh &m, const D
   launch_tile_t<float>(p, wide, write_rhs, m, tl, s, ph, c);
 }
 void prepare_tile_f32() { prepare_tile_t<float>(); }
+void launch_copy_means_f32(int p, int ne, const double *u, void *mean, cudaStream_t s) {
+  launch_copy_means_t<float>(p, ne, u, mean, s);
+}
 
 }  // namespace dg
