@@ -49,7 +49,8 @@
  *     shifted so that the mean normal discharge of the two traces is the inflow -q_in;
  *   - rain R (Eq. SWE): a uniform rate in the continuity equation;
  *   - hurricane: Holland (1980) pressure and gradient wind, Garratt (1977) drag.
- * Partly pinned: slope limiter and wet/dry (invariants and one hand-worked example each).
+ * Partly pinned: slope limiter (invariants, a hand-worked example and a recomputation from the
+ * mesh geometry) and wet/dry (invariants and hand-worked examples).
  *
  * Compile: gcc -O2 -ffp-contract=off -fPIC -shared (optionally -fopenmp).
  */

@@ -242,3 +242,102 @@ def test_wetdry_edge_rule_worked_example():
             assert L[0, 0, 1] > 1e-6 and L[0, 0, 0] < -1e-9   # mass leaves A, enters B
         else:
             assert L[0, 0, 1] == 0.0 and abs(L[0, 0, 0]) < 1e-15
+
+
+def _limit_from_geometry(xy, tri, u, nu=1.5):
+    """The Cockburn-Shu limiter of every element (p = 1), recomputed from the coordinates alone.
+
+    Independent of the oracle's preprocessing: neighbours come from shared vertex pairs, the
+    barycentre directions and boundary mirror images from vector geometry, each edge midpoint's
+    decomposition from numpy.linalg.solve (pairs tried in the stated order (i,i+1), (i+2,i),
+    (i+1,i+2); none gives no slope bound), midpoint values from scipy's basis table MID, and the
+    rebuilt linear modes from a 2x2 solve through the midpoints of edges 0 and 1.  Also returns
+    the largest number of admissible pairs found for one midpoint.
+    """
+    ne = tri.shape[0]
+    nbr = -np.ones((ne, 3), dtype=int)
+    seen = {}
+    for e in range(ne):
+        for l in range(3):
+            key = tuple(sorted((int(tri[e, (l + 1) % 3]), int(tri[e, (l + 2) % 3]))))
+            if key in seen:
+                f, lf = seen.pop(key)
+                nbr[e, l], nbr[f, lf] = f, e
+            else:
+                seen[key] = (e, l)
+    bary = xy[tri].mean(axis=1)
+    rebuild = np.linalg.inv(MID[:2, 1:])  # midpoint deviations of edges 0, 1 -> (psi_10, psi_01)
+    out = u.copy()
+    most = 0
+    for e in range(ne):
+        P, b0 = xy[tri[e]], bary[e]
+        mids, dirs = [], []
+        for l in range(3):
+            A, B = P[(l + 1) % 3], P[(l + 2) % 3]
+            mids.append(0.5 * (A + B) - b0)
+            if nbr[e, l] >= 0:
+                dirs.append(bary[nbr[e, l]] - b0)
+            else:
+                t = (B - A) / np.linalg.norm(B - A)
+                foot = A + t * np.dot(b0 - A, t)
+                dirs.append(2.0 * (foot - b0))
+        weights = []
+        for i in range(3):
+            admissible = []
+            for j1, j2 in ((i, (i + 1) % 3), ((i + 2) % 3, i), ((i + 1) % 3, (i + 2) % 3)):
+                M = np.column_stack([dirs[j1], dirs[j2]])
+                if abs(np.linalg.det(M)) < 1e-12 * np.linalg.norm(M) ** 2:
+                    continue
+                a = np.linalg.solve(M, mids[i])
+                if a.min() >= -1e-10:
+                    admissible.append((j1, j2, a))
+            most = max(most, len(admissible))
+            weights.append(admissible[0] if admissible else None)
+        for v in range(3):
+            ub = u[v, 0, e]
+            means = [u[v, 0, nbr[e, l]] if nbr[e, l] >= 0 else ub for l in range(3)]
+            dev = MID[:, 1:] @ u[v, 1:3, e]
+            d = np.empty(3)
+            for i in range(3):
+                bound = 0.0
+                if weights[i] is not None:
+                    j1, j2, a = weights[i]
+                    bound = a[0] * (means[j1] - ub) + a[1] * (means[j2] - ub)
+                x, y = dev[i], nu * bound
+                d[i] = min(x, y) if (x > 0 and y > 0) else (max(x, y) if (x < 0 and y < 0) else 0.0)
+            if np.all(d == dev):
+                continue
+            pos, neg = d[d > 0].sum(), -d[d < 0].sum()
+            tp = min(1.0, neg / pos) if pos > 0 else 0.0
+            tm = min(1.0, pos / neg) if neg > 0 else 0.0
+            dh = np.where(d > 0, tp * d, np.where(d < 0, tm * d, 0.0))
+            out[v, 1:3, e] = rebuild @ dh[:2]
+    return out, most
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_limiter_equals_geometric_recomputation_on_skewed_mesh(seed):
+    """On a jittered mesh (non-aligned neighbours, skewed cones, boundary mirrors on every side)
+    the oracle's limiter equals the recomputation from coordinates, element by element.  Every
+    midpoint there has exactly one admissible neighbour pair, so the order of trial never decides;
+    the boundary mirror rule does (a shifted mirror image, or a zero mean behind a boundary edge,
+    fails this test)."""
+    mesh = synth.grid_mesh(12, 9, 12e3, 9e3, seed=seed, jitter=0.3)
+    hb = np.full(mesh.n_nodes, 20.0)
+    prm = synth.default_params(limiter=1)
+    rng = np.random.default_rng(seed)
+    ne = mesh.n_elems
+    u = np.zeros((3, 3, ne))
+    u[:, 0] = rng.standard_normal((3, ne)) * np.array([0.5, 2.0, 2.0])[:, None]
+    u[:, 1:3] = rng.standard_normal((3, 2, ne)) * np.array([0.4, 1.5, 1.5])[:, None, None]
+    o = oracle.Oracle(mesh, hb, prm, init_modal=u)
+    o.set_state(u)
+    o.apply_limiter()
+    got = o.state()
+    want, most = _limit_from_geometry(mesh.xy, mesh.tri, u)
+    assert most == 1
+    changed = np.any(want[:, 1:3] != u[:, 1:3], axis=1)
+    assert changed.sum() > ne // 2                      # most variables were limited
+    assert np.array_equal(got[:, 0], u[:, 0])           # means kept
+    scale = np.abs(u[:, 1:3]).max()
+    assert np.abs(got - want).max() <= 1e-12 * scale
