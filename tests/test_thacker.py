@@ -1,0 +1,90 @@
+"""Thacker's (1981) planar solution in a parabolic bowl: a closed-form pin of the wetting/drying
+treatment with a moving shoreline (the paper's WETDRY kernel and the edge rule, §5.2.3).
+
+In the bowl h_b = D0 (1 - r^2/L^2) the water body keeps the bowl's shape and slides rigidly:
+its centre sits at x_c(t) = eta cos(w t), w = sqrt(2 g D0) / L, the velocity is uniform,
+u = -eta w sin(w t), and the surface is the plane
+    zeta(x, t) = (2 D0 eta / L^2) x cos(w t) - (D0 eta^2 / L^2) cos^2(w t)
+wherever the depth zeta + h_b is positive (derived from the inviscid equations: u_t + g zeta_x = 0
+and zeta_t + (H u)_x = 0 hold identically).  After half a period the body has moved 2 eta across
+the bowl, its shoreline wetting one side and drying the other.  The oracle's element means in the
+wet interior must converge to the plane on refinement; on the GPU the FP64 form must match the
+oracle through the moving front, and the FP32-mixed form must track the plane as closely.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_21208_gb300 import synth
+
+G, D0, L, ETA, H0 = 9.81, 10.0, 10e3, 1000.0, 0.01
+W = np.sqrt(2.0 * G * D0) / L
+
+
+def exact_zeta(x, t):
+    return (2.0 * D0 * ETA / L**2) * x * np.cos(W * t) - (D0 * ETA**2 / L**2) * np.cos(W * t) ** 2
+
+
+def bowl(x, y):
+    return D0 * (1.0 - (x**2 + y**2) / L**2)
+
+
+def bowl_case(n, precision=synth.FP64):
+    """The square [-1.5 L, 1.5 L]^2 (land walls) holding the bowl, the body at its t = 0 place."""
+    mesh = synth.grid_mesh(n, n, 3.0 * L, 3.0 * L, seed=5, jitter=0.2)
+    mesh.xy[:] -= 1.5 * L
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    hb = bowl(x, y)
+    init = np.zeros((3, mesh.n_nodes))
+    init[0] = np.maximum(exact_zeta(x, 0.0), H0 - hb)  # dry land rests at depth h0
+    return mesh, hb, synth.default_params(limiter=1, h0=H0, precision=precision), init
+
+
+def wet_interior_error(mesh, u, t):
+    """Mean and max |zeta_00 - zeta_exact| over elements whose exact depth exceeds 0.5 m."""
+    c = mesh.xy[mesh.tri].mean(axis=1)  # the plane's element mean is its barycentre value
+    ze = exact_zeta(c[:, 0], t)
+    wet = ze + bowl(c[:, 0], c[:, 1]) > 0.5
+    err = np.abs(u[0, 0] - ze)[wet]
+    return err.mean(), err.max(), np.abs(ze[wet]).max()
+
+
+def half_period_error(n):
+    mesh, hb, prm, init = bowl_case(n)
+    o = oracle.Oracle(mesh, hb, prm, init_nodal=init)
+    steps = int(round(np.pi / W / o.dt))
+    o.step(steps)
+    return wet_interior_error(mesh, o.state(), steps * o.dt)
+
+
+def test_thacker_planar_oscillation_converges():
+    m24, x24, amp = half_period_error(24)
+    m48, x48, _ = half_period_error(48)
+    assert amp > 1.5                      # the plane spans metres: a body left in place is far off
+    assert m48 < 0.08 and x48 < 0.35      # measured 0.051 and 0.25 m (0.018 and 0.091 at n = 96)
+    assert m24 / m48 > 2.0 and x24 / x48 > 2.0   # convergence faster than first order in h
+
+
+@pytest.mark.gpu
+def test_thacker_gpu_fp64_matches_oracle_and_mixed_tracks_the_plane():
+    from paper_2508_21208_gb300 import Model
+
+    mesh, hb, prm, init = bowl_case(48)
+    ref = oracle.Oracle(mesh, hb, prm, init_nodal=init)
+    gpu = Model(mesh, hb, prm, init_nodal=init)
+    assert abs(gpu.dt - ref.dt) <= 1e-14 * ref.dt
+    steps = int(round(np.pi / W / ref.dt))
+    ref.step(steps)
+    gpu.step(steps)
+    a, b = gpu.state(), ref.state()
+    for v in range(3):
+        assert np.linalg.norm(a[v] - b[v]) <= 1e-12 * np.linalg.norm(b[v]), v
+    assert np.array_equal(gpu.flags(), ref.flags())
+    _, _, prm32, _ = bowl_case(48, precision=synth.FP32_MIXED)
+    mixed = Model(mesh, hb, prm32, init_nodal=init)
+    mixed.step(steps)
+    m64, x64, _ = wet_interior_error(mesh, b, steps * ref.dt)
+    m32, x32, _ = wet_interior_error(mesh, mixed.state(), steps * ref.dt)
+    print(f"STATED thacker n=48 steps={steps}: FP64 mean/max {m64:.4f}/{x64:.4f} m, "
+          f"mixed {m32:.4f}/{x32:.4f} m")
+    assert m32 < 1.05 * m64 + 1e-3 and x32 < 1.05 * x64 + 1e-3
