@@ -7,8 +7,9 @@ CPU-baseline leg of ``bench.py`` may import this package.  The product
 The C source follows the paper's Sec. 2 (model and DG formulation) and
 Algorithms 1-3 (AREA, EDGE, GATHER); see its header for the readings taken
 where the paper is silent.  Partly pinned: the slope limiter and the wet/dry
-treatment are checked through invariants and hand-worked examples (and the
-limiter against a recomputation from the mesh geometry).
+treatment are checked through invariants and hand-worked examples (the limiter
+also against a recomputation from the mesh geometry, wet/dry also against
+Thacker's moving-shoreline solution in a parabolic bowl).
 """
 from __future__ import annotations
 

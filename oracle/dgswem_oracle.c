@@ -50,7 +50,8 @@
  *   - rain R (Eq. SWE): a uniform rate in the continuity equation;
  *   - hurricane: Holland (1980) pressure and gradient wind, Garratt (1977) drag.
  * Partly pinned: slope limiter (invariants, a hand-worked example and a recomputation from the
- * mesh geometry) and wet/dry (invariants and hand-worked examples).
+ * mesh geometry) and wet/dry (invariants, hand-worked examples and convergence to Thacker's
+ * moving-shoreline solution in a parabolic bowl).
  *
  * Compile: gcc -O2 -ffp-contract=off -fPIC -shared (optionally -fopenmp).
  */
