@@ -423,3 +423,43 @@ def test_edge_counts_of_grid_mesh():
         o = oracle.Oracle(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal)
         assert o.n_edges == 3 * n * n + 2 * n
         assert o.n_edges - o.n_interior == 4 * n
+
+
+def _gradient_balance_residual(ncell, lat=28.0, rho_a=1.15, rho_w=1000.0):
+    """Largest |V^2/r + f V - (1/rho_a) dp/dr| / max|(1/rho_a) dp/dr| along a line of nodes 5-300 km
+    from a stationary vortex: V from the oracle's surface stress inverted through the Garratt drag
+    law (|U| = 0.9 V), dp/dr by central differences of its pressure anomaly (node spacing
+    295.5 km / ncell).  Also returns the largest V."""
+    from scipy.optimize import brentq
+
+    mesh = synth.grid_mesh(ncell, 1, 300e3 - 4.5e3, 50.0, 0)
+    mesh.xy[:, 0] += 5e3
+    prm = synth.default_params(hurricane=1, pc_hpa=950.0, pn_hpa=1013.0, rmax_m=40e3, holland_b=1.5,
+                               vt_ms=0.0, track_x0=0.0, track_y0=0.0, coriolis_lat_deg=lat,
+                               rho_air=rho_a, rho_water=rho_w)
+    F = oracle.Oracle(mesh, np.full(mesh.n_nodes, 100.0), prm).forcing(0.0)
+    line = np.where(mesh.xy[:, 1] == 0.0)[0]
+    line = line[np.argsort(mesh.xy[line, 0])]
+    r = mesh.xy[line, 0]
+    tx, ty, pa = F[0, line], F[1, line], F[2, line]
+    assert np.all(np.abs(tx) <= 1e-12 * np.abs(ty)) and np.all(ty > 0)  # tangential, counter-clockwise
+    f = 2 * 7.2921e-5 * math.sin(math.radians(lat))
+
+    def surface_wind(kk):  # C_d(|U|) |U|^2 = kk
+        return brentq(lambda u: min(0.75 + 0.067 * u, 3.5) * 1e-3 * u * u - kk, 0.0, 200.0, xtol=1e-14)
+
+    V = np.array([surface_wind(kk) for kk in ty * rho_w / rho_a]) / 0.9
+    rhs = rho_w * (pa[2:] - pa[:-2]) / (r[2:] - r[:-2]) / rho_a  # p - pn = rho_w * anomaly
+    lhs = V[1:-1] ** 2 / r[1:-1] + f * V[1:-1]
+    return np.abs(lhs - rhs).max() / np.abs(rhs).max(), V.max()
+
+
+def test_holland_wind_and_pressure_in_gradient_balance():
+    """The vortex's wind and pressure fields satisfy the gradient-wind balance at every radius:
+    Holland's gradient wind is the positive root of V^2 / r + f V = (1/rho_a) dp/dr.  The residual
+    is the central differences' truncation error: it shrinks fourfold when the spacing halves."""
+    coarse, _ = _gradient_balance_residual(985)
+    fine, vmax = _gradient_balance_residual(1970)
+    assert fine < 1e-4                    # measured 6.7e-5 (2.7e-4 at twice the spacing)
+    assert coarse / fine > 3.5            # second-order differencing error, not a model mismatch
+    assert vmax > 40.0                    # a hurricane-strength vortex
