@@ -21,9 +21,11 @@ def _mesh_area(mesh):
 
 
 # ------------------------------------------------------------------ lake at rest
+@pytest.mark.parametrize("p", [1, 2])
 @pytest.mark.parametrize("zeta0", [0.0, 0.3])
-def test_lake_at_rest_rhs_and_200_steps(zeta0):
+def test_lake_at_rest_rhs_and_200_steps(zeta0, p):
     c = synth.config1(lake=True)
+    c.params["p"] = p
     c.init_nodal[0] = zeta0
     o = oracle.Oracle(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal)
     r = o.rhs(0.0)
@@ -35,8 +37,10 @@ def test_lake_at_rest_rhs_and_200_steps(zeta0):
     assert np.abs(u[0, 0] - zeta0).max() < 1e-12
 
 
-def test_mass_conserved_all_land_200_steps():
+@pytest.mark.parametrize("p", [1, 2])
+def test_mass_conserved_all_land_200_steps(p):
     c = synth.config1()
+    c.params["p"] = p
     o = oracle.Oracle(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal)
     m0, v0 = o.mass()
     o.step(200)
@@ -45,8 +49,9 @@ def test_mass_conserved_all_land_200_steps():
     assert abs(m1 - m0) <= 1e-14 * v0
 
 
-def test_mass_conserved_with_wetdry_and_limiter():
-    c = synth.config2(n=24)
+@pytest.mark.parametrize("p", [1, 2])
+def test_mass_conserved_with_wetdry_and_limiter(p):
+    c = synth.config2(n=24, p=p)
     c.mesh.bedge_type[:] = synth.BC_LAND  # closed basin
     c.params["tide_amp"] = 0.0
     # a slope-driven wave running up the shore
@@ -80,8 +85,10 @@ def _mirrored_config1(n=20):
     return c
 
 
-def test_mirror_symmetry_about_x():
+@pytest.mark.parametrize("p", [1, 2])
+def test_mirror_symmetry_about_x(p):
     c = _mirrored_config1()
+    c.params["p"] = p
     o = oracle.Oracle(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal)
     o.step(50)
     u = o.state()
