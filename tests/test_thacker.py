@@ -50,19 +50,21 @@ def wet_interior_error(mesh, u, t):
     return err.mean(), err.max(), np.abs(ze[wet]).max()
 
 
-def half_period_error(n):
+def half_period_error(n, flux=0):
     mesh, hb, prm, init = bowl_case(n)
+    prm["flux"] = flux
     o = oracle.Oracle(mesh, hb, prm, init_nodal=init)
     steps = int(round(np.pi / W / o.dt))
     o.step(steps)
     return wet_interior_error(mesh, o.state(), steps * o.dt)
 
 
-def test_thacker_planar_oscillation_converges():
-    m24, x24, amp = half_period_error(24)
-    m48, x48, _ = half_period_error(48)
+@pytest.mark.parametrize("flux", [0, 1])  # LLF, Roe
+def test_thacker_planar_oscillation_converges(flux):
+    m24, x24, amp = half_period_error(24, flux)
+    m48, x48, _ = half_period_error(48, flux)
     assert amp > 1.5                      # the plane spans metres: a body left in place is far off
-    assert m48 < 0.08 and x48 < 0.35      # measured 0.051 and 0.25 m (0.018 and 0.091 at n = 96)
+    assert m48 < 0.08 and x48 < 0.35      # LLF 0.051 and 0.25 m (0.018, 0.091 at n = 96); Roe 0.043, 0.23
     assert m24 / m48 > 2.0 and x24 / x48 > 2.0   # convergence faster than first order in h
 
 
