@@ -8,6 +8,7 @@ ahead of which the water is still.  This wave is a fixed point of the boundary t
 means behind its front converge to it at the method's order.
 """
 import numpy as np
+import pytest
 
 import oracle
 from paper_2508_21208_gb300 import synth
@@ -17,10 +18,10 @@ W, C = 2.0 * np.pi / PERIOD, np.sqrt(G * D)
 LX, LY, T_END = 80e3, 5e3, 5000.0
 
 
-def mean_error(nx):
+def mean_error(nx, flux=0):
     """Mean |zeta_00 - zeta_exact| / A over elements at least 3 cells behind the front."""
     mesh = synth.grid_mesh(nx, max(2, nx // 16), LX, LY, seed=7, jitter=0.2, open_sides=("left",))
-    prm = synth.default_params(tide_amp=A, tide_period=PERIOD)
+    prm = synth.default_params(tide_amp=A, tide_period=PERIOD, flux=flux)
     o = oracle.Oracle(mesh, np.full(mesh.n_nodes, D), prm, init_nodal=np.zeros((3, mesh.n_nodes)))
     steps = int(round(T_END / o.dt))
     o.step(steps)
@@ -33,10 +34,11 @@ def mean_error(nx):
             np.abs(u[1, 0] - C * ze)[behind].mean() / (C * A))
 
 
-def test_tidal_wave_converges_at_second_order():
-    e = [mean_error(nx) for nx in (32, 64, 128)]
+@pytest.mark.parametrize("flux", [0, 1])  # LLF, Roe
+def test_tidal_wave_converges_at_second_order(flux):
+    e = [mean_error(nx, flux) for nx in (32, 64, 128)]
     z = [a for a, _ in e]
     q = [b for _, b in e]
-    assert z[2] < 1e-3 and q[2] < 1e-3          # measured 6.6e-4 and 7.2e-4 of the amplitude
-    for k in range(2):                          # measured ratios 3.4 (zeta) and 3.4 (q)
+    assert z[2] < 1e-3 and q[2] < 1e-3          # LLF 6.6e-4 and 7.2e-4 of the amplitude; Roe 4.6e-4
+    for k in range(2):                          # measured ratios 3.4 (LLF) and 3.6-3.8 (Roe)
         assert z[k] / z[k + 1] > 2.5 and q[k] / q[k + 1] > 2.5
