@@ -148,6 +148,23 @@ def test_thacker_gpu_fp64_matches_oracle_and_mixed_tracks_the_plane():
 
 
 @pytest.mark.gpu
+def test_thacker_roe_gpu_fp64_matches_oracle():
+    from paper_2508_21208_gb300 import Model
+
+    mesh, hb, prm, init = bowl_case(32)
+    prm["flux"] = 1
+    ref = oracle.Oracle(mesh, hb, prm, init_nodal=init)
+    gpu = Model(mesh, hb, prm, init_nodal=init)
+    steps = int(round(np.pi / W / ref.dt))
+    ref.step(steps)
+    gpu.step(steps)
+    a, b = gpu.state(), ref.state()
+    for v in range(3):
+        assert np.linalg.norm(a[v] - b[v]) <= 1e-12 * np.linalg.norm(b[v]), v
+    assert np.array_equal(gpu.flags(), ref.flags())
+
+
+@pytest.mark.gpu
 def test_thacker_rotating_gpu_fp64_matches_oracle():
     from paper_2508_21208_gb300 import Model
 
