@@ -50,21 +50,23 @@ def wet_interior_error(mesh, u, t):
     return err.mean(), err.max(), np.abs(ze[wet]).max()
 
 
-def half_period_error(n, flux=0):
+def half_period_error(n, flux=0, p=1):
     mesh, hb, prm, init = bowl_case(n)
     prm["flux"] = flux
-    o = oracle.Oracle(mesh, hb, prm, init_nodal=init)
+    prm["p"] = p
+    o = oracle.Oracle(mesh, hb, prm, init_nodal=init, omp=True)  # bitwise the serial build
     steps = int(round(np.pi / W / o.dt))
     o.step(steps)
     return wet_interior_error(mesh, o.state(), steps * o.dt)
 
 
-@pytest.mark.parametrize("flux", [0, 1])  # LLF, Roe
-def test_thacker_planar_oscillation_converges(flux):
-    m24, x24, amp = half_period_error(24, flux)
-    m48, x48, _ = half_period_error(48, flux)
+@pytest.mark.parametrize("flux,p", [(0, 1), (1, 1), (0, 2)])  # LLF / Roe at p = 1, LLF at p = 2
+def test_thacker_planar_oscillation_converges(flux, p):
+    m24, x24, amp = half_period_error(24, flux, p)
+    m48, x48, _ = half_period_error(48, flux, p)
     assert amp > 1.5                      # the plane spans metres: a body left in place is far off
-    assert m48 < 0.08 and x48 < 0.35      # LLF 0.051 and 0.25 m (0.018, 0.091 at n = 96); Roe 0.043, 0.23
+    assert m48 < 0.08 and x48 < 0.35      # LLF 0.051, 0.25 m (0.018, 0.091 at n = 96); Roe 0.043, 0.23;
+                                          # p = 2 0.051, 0.23 (the front bounds the order)
     assert m24 / m48 > 2.0 and x24 / x48 > 2.0   # convergence faster than first order in h
 
 
@@ -102,7 +104,7 @@ def rotating_case(n, lat_deg=90.0, precision=synth.FP64):
 
 def rotating_error(n):
     mesh, hb, prm, init, zeta, s = rotating_case(n)
-    o = oracle.Oracle(mesh, hb, prm, init_nodal=init)
+    o = oracle.Oracle(mesh, hb, prm, init_nodal=init, omp=True)
     steps = int(round(np.pi / s / o.dt))  # half a turn
     o.step(steps)
     t = steps * o.dt
