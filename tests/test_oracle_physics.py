@@ -470,3 +470,20 @@ def test_holland_wind_and_pressure_in_gradient_balance():
     assert fine < 1e-4                    # measured 6.7e-5 (2.7e-4 at twice the spacing)
     assert coarse / fine > 3.5            # second-order differencing error, not a model mismatch
     assert vmax > 40.0                    # a hurricane-strength vortex
+
+
+def test_openmp_build_is_bitwise_the_serial_build():
+    """The oracle's OpenMP build (used for the large cases and the CPU baseline) parallelises
+    only loops whose iterations write disjoint data, so it reproduces the serial build exactly."""
+    c = synth.config2(n=24)
+    c.params["hurricane"] = 1
+    c.params["coriolis"] = 1
+    c.params["coriolis_lat_deg"] = 28.0
+    runs = []
+    for omp in (False, True):
+        o = oracle.Oracle(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, omp=omp)
+        o.step(60)
+        runs.append((o.state(), o.flags(), o.mass()))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2] == runs[1][2]
