@@ -5,8 +5,14 @@
 #include <mutex>
 
 #include "../../include/dgswem.h"
+#include "compsum.cuh"
 
 namespace {
+
+using dg::Comp;
+using dg::comp_add;
+using dg::comp_block_reduce;
+using dg::comp_merge;
 
 constexpr int kThreads = 256;
 constexpr int kPerBlock = kThreads * 8;  // elements summed by one block
@@ -21,47 +27,17 @@ static __device__ __align__(256) double g_partials[4 * kMaxBlocks];
 std::mutex g_lock;
 double *g_addr[kMaxDevices] = {};
 
-struct Pair {
-  double s, c;
-};
-__device__ __forceinline__ void add(Pair &a, double x) {  // Neumaier step
-  const double t = a.s + x;
-  a.c += fabs(a.s) >= fabs(x) ? (a.s - t) + x : (x - t) + a.s;
-  a.s = t;
-}
-__device__ __forceinline__ Pair merge(Pair a, Pair b) {
-  add(a, b.s);
-  a.c += b.c;
-  return a;
-}
-
-__device__ void block_reduce(Pair &a, Pair &b) {
-  __shared__ Pair sa[kThreads], sb[kThreads];
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  __syncthreads();
-  for (int w = kThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      sa[threadIdx.x] = merge(sa[threadIdx.x], sa[threadIdx.x + w]);
-      sb[threadIdx.x] = merge(sb[threadIdx.x], sb[threadIdx.x + w]);
-    }
-    __syncthreads();
-  }
-  a = sa[0];
-  b = sb[0];
-}
-
 __global__ void __launch_bounds__(kThreads) k_partials(const double *z, const double *area, const double *hb,
                                                         int n, double *partials) {
-  Pair a{0.0, 0.0}, b{0.0, 0.0};
+  Comp a{0.0, 0.0}, b{0.0, 0.0};
   const int base = blockIdx.x * kPerBlock;
   for (int i = threadIdx.x; i < kPerBlock; i += kThreads) {
     const int e = base + i;
     if (e >= n) break;
-    add(a, area[e] * z[e]);
-    add(b, area[e] * (z[e] + hb[e]));
+    comp_add(a, area[e] * z[e]);
+    comp_add(b, area[e] * (z[e] + hb[e]));
   }
-  block_reduce(a, b);
+  comp_block_reduce<kThreads>(a, b);
   if (threadIdx.x == 0) {
     partials[4 * blockIdx.x + 0] = a.s;
     partials[4 * blockIdx.x + 1] = a.c;
@@ -71,19 +47,21 @@ __global__ void __launch_bounds__(kThreads) k_partials(const double *z, const do
 }
 
 __global__ void __launch_bounds__(kThreads) k_total(int nb, const double *partials, double *out) {
-  Pair a{0.0, 0.0}, b{0.0, 0.0};
+  Comp a{0.0, 0.0}, b{0.0, 0.0};
   for (int i = threadIdx.x; i < nb; i += kThreads) {
-    a = merge(a, Pair{partials[4 * i], partials[4 * i + 1]});
-    b = merge(b, Pair{partials[4 * i + 2], partials[4 * i + 3]});
+    a = comp_merge(a, Comp{partials[4 * i], partials[4 * i + 1]});
+    b = comp_merge(b, Comp{partials[4 * i + 2], partials[4 * i + 3]});
   }
-  block_reduce(a, b);
+  comp_block_reduce<kThreads>(a, b);
   if (threadIdx.x == 0) {
     out[0] = a.s + a.c;
     out[1] = b.s + b.c;
   }
 }
 
-// Device address of the static buffer on the current device, looked up once per device.
+// Device address of the static buffer on the current device, looked up once per device and kept
+// for the life of the process: this assumes the device's primary context is not reset
+// (cudaDeviceReset) or destroyed while the library is loaded.
 int scratch_address(double **ptr) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DGSWEM_ECUDA;

@@ -166,3 +166,21 @@ def test_ensemble_step_refuses_a_single_model_context(lib):
     assert rc == 0
     assert lib.dgswem_ensemble_step(h, 1) == -1
     lib.dgswem_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["one byte short", "null"])
+def test_attach_with_a_short_workspace_is_enomem(lib, kind):
+    """Allocator failure simulated by a size cap: a workspace one byte smaller than
+    dgswem_workspace_size (or none) is refused with DGSWEM_ENOMEM, and the error is sticky.  The
+    size check comes before any device work, so the (never dereferenced) address below is safe and
+    no GPU is needed."""
+    c = synth.config1(n=8)
+    rc, h = _create(c.mesh, c.bathy, c.params)
+    assert rc == 0
+    n = C.c_size_t()
+    assert lib.dgswem_workspace_size(h, C.byref(n)) == 0
+    addr = C.c_void_p(1 << 20) if kind == "one byte short" else C.c_void_p(0)
+    assert lib.dgswem_attach(h, addr, n.value - 1, None) == -7
+    assert b"workspace" in lib.dgswem_last_error(h)
+    assert lib.dgswem_step(h, 1) == -7  # sticky
+    lib.dgswem_destroy(h)

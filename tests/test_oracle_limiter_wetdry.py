@@ -244,7 +244,10 @@ def test_wetdry_edge_rule_worked_example():
             assert L[0, 0, 1] == 0.0 and abs(L[0, 0, 0]) < 1e-15
 
 
-def _limit_from_geometry(xy, tri, u, nu=1.5):
+PAIR_ORDER = ((0, 1), (2, 0), (1, 2))  # (i, i+1), (i+2, i), (i+1, i+2) as offsets from i
+
+
+def _limit_from_geometry(xy, tri, u, nu=1.5, order=PAIR_ORDER):
     """The Cockburn-Shu limiter of every element (p = 1), recomputed from the coordinates alone.
 
     Independent of the oracle's preprocessing: neighbours come from shared vertex pairs, the
@@ -284,7 +287,8 @@ def _limit_from_geometry(xy, tri, u, nu=1.5):
         weights = []
         for i in range(3):
             admissible = []
-            for j1, j2 in ((i, (i + 1) % 3), ((i + 2) % 3, i), ((i + 1) % 3, (i + 2) % 3)):
+            for o1, o2 in order:
+                j1, j2 = (i + o1) % 3, (i + o2) % 3
                 M = np.column_stack([dirs[j1], dirs[j2]])
                 if abs(np.linalg.det(M)) < 1e-12 * np.linalg.norm(M) ** 2:
                     continue
@@ -341,3 +345,47 @@ def test_limiter_equals_geometric_recomputation_on_skewed_mesh(seed):
     assert np.array_equal(got[:, 0], u[:, 0])           # means kept
     scale = np.abs(u[:, 1:3]).max()
     assert np.abs(got - want).max() <= 1e-12 * scale
+
+
+def test_limiter_pair_order_worked_example():
+    """The order in which neighbour pairs are tried decides, worked by hand.
+
+    Centre element A(0,0) B(12,0) C(5,1) (km), barycentre b0 = (17/3, 1/3); neighbours across
+    BC, CA and AB have third vertices (16,4), (13,8) and (9,-3), so the barycentre directions are
+    d0 = (16/3, 4/3), d1 = (1/3, 8/3), d2 = (4/3, -4/3).  The midpoint of edge 0 (BC), at
+    m0 - b0 = (17/6, 1/6), decomposes with non-negative weights along two pairs:
+    (d2, d0) with (13/40, 9/20) and (d1, d2) with (1, 15/8); the pair (d0, d1) fails (-13/62).
+    Tried in the order (i,i+1), (i+2,i), (i+1,i+2), edge 0 takes (d2, d0).  Edge 1 has no
+    admissible pair (its bound is 0); edge 2 has two that both put 1/4 on d2 alone.
+
+    Surface: centre mean 0 and linear modes (0.2, 0.6), i.e. midpoint deviations 0.4, 0.2, -0.6;
+    neighbour means 1.0, 0.0, -0.8.  Bounds (nu = 1.5): edge 0, 1.5 (13/40 (-0.8) + 9/20 (1.0)) =
+    0.285; edge 1, 0; edge 2, 1.5 (1/4)(-0.8) = -0.3.  minmod: 0.285, 0, -0.3; their sum is
+    negative, so the negative part is scaled by 0.285/0.3: deviations 0.285, 0, -0.285, i.e.
+    linear modes (0.285, 0.285).  With (d1, d2) at edge 0 the bound there would be
+    1.5 (1 (0.0) + 15/8 (-0.8)) = -2.25, minmod 0, and the element would be flattened.
+    """
+    km = 1000.0
+    xy = np.array([[0, 0], [12, 0], [5, 1], [16, 4], [13, 8], [9, -3]], float) * km
+    tri = np.array([[0, 1, 2], [2, 1, 3], [0, 2, 4], [1, 0, 5]], np.int32)
+    bedge = np.array([[1, 3], [3, 2], [2, 4], [4, 0], [0, 5], [5, 1]], np.int32)
+    mesh = synth.Mesh(xy, tri, bedge, np.zeros(6, np.int32))
+    hb = np.full(6, 20.0)
+    prm = synth.default_params(limiter=1)
+    u = np.zeros((3, 3, 4))
+    u[0, :, 0] = [0.0, 0.2, 0.6]
+    u[0, 0, 1:] = [1.0, 0.0, -0.8]
+    assert np.allclose(MID[:, 1:] @ u[0, 1:3, 0], [0.4, 0.2, -0.6], atol=1e-15)
+    o = oracle.Oracle(mesh, hb, prm, init_modal=u)
+    o.set_state(u)
+    o.apply_limiter()
+    got = o.state()
+    assert np.allclose(got[0, :, 0], [0.0, 0.285, 0.285], rtol=0, atol=1e-14)
+    # the recomputation from coordinates agrees in the stated order and differs in any order that
+    # tries (i+1, i+2) before (i+2, i)
+    want, most = _limit_from_geometry(mesh.xy, mesh.tri, u)
+    assert most == 2
+    assert np.allclose(want[0, :, 0], got[0, :, 0], rtol=0, atol=1e-14)
+    for order in (((0, 1), (1, 2), (2, 0)), ((1, 2), (2, 0), (0, 1))):
+        alt, _ = _limit_from_geometry(mesh.xy, mesh.tri, u, order=order)
+        assert np.allclose(alt[0, 1:3, 0], [0.0, 0.0], atol=1e-14)

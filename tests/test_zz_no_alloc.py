@@ -4,10 +4,12 @@ Some callers cannot let a library call cudaMalloc: a host model or coupler that 
 whole memory budget, or a time-critical loop that cannot afford an allocation's implicit
 synchronisation or failure.  This entry point takes only the caller's own device arrays and keeps
 its partial sums in a fixed buffer inside the library.  The test checks it against dgswem_mass of
-a running model on two calls in a row (the shared buffer must not carry anything over), and that
-an oversized input is refused.  The file is named so that pytest collects it last.
+a running model on two calls in a row (the shared buffer must not carry anything over), checks a
+ragged element count against an exactly rounded host sum, and checks that null pointers, an empty
+input and an oversized input are refused.  The file is named so that pytest collects it last.
 """
 import ctypes as C
+import math
 
 import numpy as np
 import pytest
@@ -49,6 +51,31 @@ def test_noalloc_mass_matches_context_mass_twice():
         # same sums in a different element order: equal to rounding of the compensated sums
         assert abs(got_vol - ref_vol) <= 1e-14 * ref_vol
         assert abs(got_mass - ref_mass) <= 1e-14 * ref_vol
+
+    # a ragged count (the last partial-sum block is partly filled, n is no multiple of 2048):
+    # the first n - 777 elements, against an exactly rounded host sum of the same terms
+    nr = n - 777
+    rc = lib.dgswem_mass_noalloc(C.c_void_p(z.data_ptr()), C.c_void_p(ar.data_ptr()),
+                                 C.c_void_p(hb.data_ptr()), nr, C.c_void_p(out.data_ptr()),
+                                 C.c_void_p(stream.cuda_stream))
+    assert rc == 0
+    stream.synchronize()
+    got_mass, got_vol = out.cpu().numpy()
+    zz, aa, hh = u[0, 0, :nr], area[:nr], hb_mean[:nr]
+    want_mass = math.fsum(aa * zz)
+    want_vol = math.fsum(aa * (zz + hh))
+    assert abs(got_mass - want_mass) <= 1e-14 * abs(want_vol)
+    assert abs(got_vol - want_vol) <= 1e-14 * abs(want_vol)
+
+    # invalid arguments are refused before any device work
+    null = C.c_void_p(0)
+    for args in ((null, ar, hb, out), (z, null, hb, out), (z, ar, null, out), (z, ar, hb, null)):
+        ptrs = [a if isinstance(a, C.c_void_p) else C.c_void_p(a.data_ptr()) for a in args]
+        assert lib.dgswem_mass_noalloc(ptrs[0], ptrs[1], ptrs[2], n, ptrs[3],
+                                       C.c_void_p(stream.cuda_stream)) == -1
+    assert lib.dgswem_mass_noalloc(C.c_void_p(z.data_ptr()), C.c_void_p(ar.data_ptr()),
+                                   C.c_void_p(hb.data_ptr()), 0, C.c_void_p(out.data_ptr()),
+                                   C.c_void_p(stream.cuda_stream)) == -1
 
     too_big = (1 << 26) + 1
     rc = lib.dgswem_mass_noalloc(C.c_void_p(z.data_ptr()), C.c_void_p(ar.data_ptr()),
