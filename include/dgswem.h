@@ -128,7 +128,7 @@ typedef struct {
   double river_q;        /* inflow discharge per unit width on DGSWEM_BC_RIVER edges (m^2/s) */
 } dgswem_params;
 
-/* numerical fluxes (Sec. 2.2: "e.g., Local Lax-Friedrichs or Roe flux") */
+/* numerical fluxes (Sec. 2.2 names local Lax-Friedrichs and Roe as choices for F^) */
 #define DGSWEM_FLUX_LLF 0 /* local Lax-Friedrichs, lambda = max(|u.n| + sqrt(gH)) of the two traces */
 #define DGSWEM_FLUX_ROE 1 /* Roe (1981): Roe-averaged |A| in the edge frame, Harten entropy fix
                              (delta = c~/10) on the two acoustic waves */
@@ -173,7 +173,9 @@ typedef struct {
 DGSWEM_API int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_params *params,
                   const dgswem_init *init, const dgswem_tuning *tuning, dgswem_ctx **out);
 
-/* Bytes of device workspace (256-byte aligned) that dgswem_attach needs. */
+/* Bytes of device workspace (256-byte aligned) that dgswem_attach needs.  No paper passage: the
+ * paper keeps its arrays in unified memory (Sec. 5.1); this library instead lets the caller
+ * provide one explicit device buffer.  Errors: DGSWEM_EINVAL (null argument). */
 DGSWEM_API int dgswem_workspace_size(const dgswem_ctx *ctx, size_t *bytes);
 
 /* Bind a caller-owned device buffer of at least dgswem_workspace_size bytes (the caller keeps
@@ -182,7 +184,11 @@ DGSWEM_API int dgswem_workspace_size(const dgswem_ctx *ctx, size_t *bytes);
  * data and the initial state,
  * applies the wetting/drying operator to the initial state, computes dt when params->dt <= 0,
  * autotunes if asked, and captures one time step as a CUDA graph.  Synchronises the stream.
- * Errors: DGSWEM_ENOMEM, DGSWEM_ECUDA, DGSWEM_ESTATE (already attached). */
+ * Replaces the paper's unified-memory placement and prefetching (Sec. 5.1, Sec. 5.2.4) with one
+ * upload; the time step follows Sec. 6.1, which runs a fixed dt for the whole simulation.
+ * Errors: DGSWEM_ENOMEM (buffer null or smaller than dgswem_workspace_size, checked before any
+ * device work), DGSWEM_EINVAL (buffer not 256-byte aligned), DGSWEM_ECUDA, DGSWEM_ESTATE (already
+ * attached). */
 DGSWEM_API int dgswem_attach(dgswem_ctx *ctx, void *d_workspace, size_t bytes, void *stream);
 
 /* Advance n_steps time steps of the chosen SSP-RK scheme (Sec. 2.2 Eq. RKSSP; SSP-RK2 by
@@ -191,48 +197,67 @@ DGSWEM_API int dgswem_attach(dgswem_ctx *ctx, void *d_workspace, size_t bytes, v
 DGSWEM_API int dgswem_step(dgswem_ctx *ctx, int32_t n_steps);
 
 /* Copy the modal state to caller-owned host arrays, each [ndof][n_elems] in the caller's
- * element order.  Any of the three pointers may be NULL.  Synchronises. */
+ * element order: the Dubiner coefficients of zeta, q_x and q_y (Sec. 2.2, Eq. dubiner; the
+ * unknowns of the weak form Eq. elem_weak_form).  Any of the three pointers may be NULL.
+ * Synchronises.  Errors: DGSWEM_ESTATE (not attached), DGSWEM_ECUDA, or a sticky device error. */
 DGSWEM_API int dgswem_get_state(dgswem_ctx *ctx, double *h_zeta, double *h_qx, double *h_qy);
 
-/* Replace the modal state (caller order, same layout as dgswem_get_state) and set the time to t
- * (the step counter restarts at 0).  Wet/dry flags are recomputed from the new state.  The
- * copies are asynchronous; the host arrays must stay valid until the next synchronising call. */
+/* Replace the modal state (caller order, same layout as dgswem_get_state: the Dubiner
+ * coefficients of Sec. 2.2, Eq. dubiner) and set the time to t (the step counter restarts at 0).
+ * Wet/dry flags are recomputed from the new state (classification of Sec. 5.2.3 WETDRY, state
+ * unchanged).  The copies are asynchronous; the host arrays must stay valid until the next
+ * synchronising call.  Errors: DGSWEM_EINVAL (null pointer, non-finite t), DGSWEM_ESTATE. */
 DGSWEM_API int dgswem_set_state(dgswem_ctx *ctx, const double *h_zeta, const double *h_qx,
                      const double *h_qy, double t);
 
 /* Total surface anomaly volume sum_e |Omega_e| zeta_e,00 and water volume
  * sum_e |Omega_e| (zeta_e,00 + mean h_b), each a compensated (Neumaier) double sum in a fixed
- * block order, hence bitwise reproducible.  Synchronises. */
+ * block order, hence bitwise reproducible.  No paper passage defines it: it is this library's
+ * conservation diagnostic for the continuity equation of Eq. SWE (with mode (0,0) the element
+ * mean, the discrete volume is exactly this sum).  Synchronises.  Errors: DGSWEM_EINVAL (null
+ * pointer), DGSWEM_ESTATE, DGSWEM_ECUDA, or a sticky device error. */
 DGSWEM_API int dgswem_mass(dgswem_ctx *ctx, double *mass_zeta, double *volume);
 
-/* Time step, current time t0 + steps*dt, and steps done since create / set_state. */
+/* Time step, current time t0 + steps*dt, and steps done since create / set_state.  The step is
+ * fixed for the run, as the paper's runs use one fixed dt (Sec. 6.1).  Any pointer may be NULL.
+ * Errors: DGSWEM_ESTATE (not attached). */
 DGSWEM_API int dgswem_info(dgswem_ctx *ctx, double *dt, double *t, int64_t *steps_done);
 
-/* Wait for the stream and surface any device-side error.  */
+/* Wait for the stream and surface any device-side error (no paper passage: the host-side
+ * counterpart of the paper's `!$acc wait`, Sec. 5.3).  Errors: the sticky error, DGSWEM_ESTATE. */
 DGSWEM_API int dgswem_sync(dgswem_ctx *ctx);
 
-/* Per-element wet/dry flags (0 wet, 1 partially wet, 2 dry), caller order.  Synchronises. */
+/* Per-element wet/dry flags (0 wet, 1 partially wet, 2 dry), caller order: the element states of
+ * the wetting/drying treatment (Sec. 5.2.3 WETDRY).  Synchronises.  Errors: DGSWEM_EINVAL (null
+ * pointer or an ensemble context: see dgswem_ensemble_get_flags), DGSWEM_ESTATE. */
 DGSWEM_API int dgswem_get_flags(dgswem_ctx *ctx, uint8_t *h_flags);
 
+/* Release the context (after synchronising its stream).  The caller's workspace and stream stay
+ * the caller's.  No paper passage. */
 DGSWEM_API void dgswem_destroy(dgswem_ctx *ctx);
+/* Text of the context's first error ("" if none; "null context" for NULL).  No paper passage. */
 DGSWEM_API const char *dgswem_last_error(const dgswem_ctx *ctx);
 
 /* ---- single operators, for checking each step of the path against a reference ----
  * Each runs the named kernel(s) once on the current state, on the context's stream, then
  * synchronises. */
 
-/* L_h(u) of Eq. RKSSP at time t (area integrals, edge fluxes, inverse mass matrix; no limiter,
- * no wet/dry), written to h_out as [3][ndof][n_elems] in caller order. */
+/* L_h(u) of Eq. RKSSP at time t (area integrals of Alg. 1, edge fluxes of Alg. 2 gathered as in
+ * Alg. 3, inverse mass matrix; no limiter, no wet/dry), written to h_out as [3][ndof][n_elems] in
+ * caller order.  In the FP32-mixed form the elements at the wetting/drying front take the double
+ * path, as in a step. */
 DGSWEM_API int dgswem_eval_rhs(dgswem_ctx *ctx, double t, double *h_out);
-/* Apply the slope limiter (SLOPELIM) to the current state in place. */
+/* Apply the slope limiter (Sec. 2.2, where limiting is optional; kernel SLOPELIM of Sec. 5.2.3) to
+ * the current state in place, every element in the form's own arithmetic. */
 DGSWEM_API int dgswem_apply_limiter(dgswem_ctx *ctx);
-/* Apply the wetting/drying operator (WETDRY) to the current state in place. */
+/* Apply the wetting/drying operator (kernel WETDRY of Sec. 5.2.3) to the current state in place.
+ * DGSWEM_EINVAL when wetting/drying is off (h0 = 0). */
 DGSWEM_API int dgswem_apply_wetdry(dgswem_ctx *ctx);
 /* Nodal forcing (WIND) at time t: h_out [3][n_nodes] = (tau_x/rho_w, tau_y/rho_w,
  * (p_a - p_n)/rho_w); the pressure anomaly, since only its gradient enters Eq. SWE. */
 DGSWEM_API int dgswem_eval_forcing(dgswem_ctx *ctx, double t, double *h_out);
 
-/* ---- kernel timing ----
+/* ---- kernel timing (no paper passage: the per-kernel times behind Sec. 6.2's breakdown) ----
  * With timing on, dgswem_step replays a graph of the same step with event-record nodes between
  * its kernels (captured on first use; both graphs are kept, so switching back and forth costs a
  * stream synchronisation only).  dgswem_kernel_times then returns, for the last replayed step,
@@ -242,11 +267,12 @@ DGSWEM_API int dgswem_eval_forcing(dgswem_ctx *ctx, double t, double *h_out);
 DGSWEM_API int dgswem_set_kernel_timing(dgswem_ctx *ctx, int32_t on);
 DGSWEM_API int dgswem_kernel_times(dgswem_ctx *ctx, float *ms, const char **names, int32_t capacity,
                         int32_t *n_kernels);
-/* Kernel launches per time step in the captured graph, and the chosen variant / block size. */
+/* Kernel launches per time step in the captured graph, and the chosen variant / block size (no
+ * paper passage).  Any pointer may be NULL.  Errors: DGSWEM_ESTATE (not attached). */
 DGSWEM_API int dgswem_graph_info(dgswem_ctx *ctx, int32_t *kernels_per_step, int32_t *variant,
                       int32_t *block);
 
-/* The autotuner's measurements at attach: for each timed candidate its variant (single model:
+/* No paper passage.  The autotuner's measurements at attach: for each timed candidate its variant (single model:
  * DGSWEM_VARIANT_*; ensemble: DGSWEM_ENSEMBLE_*), block / tile size and milliseconds per step.
  * n_entries gets the count (0 when a fixed configuration was requested). */
 DGSWEM_API int dgswem_tune_log(dgswem_ctx *ctx, int32_t *variant, int32_t *block, float *ms_per_step,
@@ -271,17 +297,81 @@ DGSWEM_API int dgswem_ensemble_create(int32_t n, const dgswem_mesh *const *meshe
                            const double *const *bathy, const dgswem_params *params,
                            const dgswem_init *inits, const dgswem_tuning *tuning,
                            dgswem_ctx **out);
-/* Advance every member n_steps of its own time step: dgswem_step on an ensemble context (one
- * replay of the captured ensemble step per step), checked to be one.  DGSWEM_EINVAL for a
- * single-model context or n_steps < 0. */
+/* Advance every member n_steps of its own time step (Sec. 2.2 Eq. RKSSP, as dgswem_step):
+ * dgswem_step on an ensemble context (one replay of the captured ensemble step per step), checked
+ * to be one.  DGSWEM_EINVAL for a single-model context or n_steps < 0. */
 DGSWEM_API int dgswem_ensemble_step(dgswem_ctx *ctx, int32_t n_steps);
+/* Member `member`'s modal state (the Dubiner coefficients of Sec. 2.2, Eq. dubiner), laid out as
+ * dgswem_get_state in that member's mesh order.  Synchronises.  DGSWEM_EINVAL for a member out of
+ * range or a single-model context. */
 DGSWEM_API int dgswem_ensemble_get_state(dgswem_ctx *ctx, int32_t member, double *h_zeta, double *h_qx,
                               double *h_qy);
+/* Member `member`'s wet/dry flags (0 wet, 1 partially wet, 2 dry; Sec. 5.2.3 WETDRY) in that
+ * member's mesh order, as dgswem_get_flags.  Synchronises.  DGSWEM_EINVAL for a null pointer, a
+ * member out of range or a single-model context. */
+DGSWEM_API int dgswem_ensemble_get_flags(dgswem_ctx *ctx, int32_t member, uint8_t *h_flags);
+/* Member `member`'s fixed time step (Sec. 6.1), time and steps done; as dgswem_info. */
 DGSWEM_API int dgswem_ensemble_info(dgswem_ctx *ctx, int32_t member, double *dt, double *t,
                          int64_t *steps_done);
-/* Test hook: when on, one block skips every grid-barrier arrival, so the other blocks' bounded
- * waits expire and the step reports DGSWEM_ETIMEOUT instead of hanging. */
+/* Test hook (no paper passage): when on, one block skips every grid-barrier arrival, so the other
+ * blocks' bounded waits expire and the step reports DGSWEM_ETIMEOUT instead of hanging.  Needs the
+ * persistent launch (DGSWEM_EINVAL otherwise). */
 DGSWEM_API int dgswem_ensemble_set_fault(dgswem_ctx *ctx, int32_t skip_arrival);
+
+/* ---- one model on several GPUs: domain decomposition (Sec. 5.3) ----
+ * The paper runs DG-SWEM on several GPUs by splitting the mesh among MPI ranks and exchanging the
+ * states of the ghost elements at the part boundaries, packed into contiguous buffers on the GPU
+ * (Sec. 5.3, Listings code:mpi and code:pack).  Here a part is one context on one GPU whose
+ * sub-mesh holds its own elements and two layers of ghost elements: the part updates its own
+ * elements and, redundantly, the first ghost layer (so that every neighbour mean its own elements'
+ * limiter needs is local), limits and wets/dries its own elements, and then receives the ghost
+ * elements' states and wet/dry flags from their owners, once per Runge-Kutta stage.  Moving the
+ * packed bytes between GPUs (NCCL send/recv, MPI, a copy) is the caller's; the library only packs
+ * and unpacks.  These host functions allocate nothing and touch no device. */
+
+/* Recursive coordinate bisection: part[e] in [0, n_parts) for every element e (caller order), the
+ * parts' element counts proportional to their share of parts at every split (the paper partitions
+ * with METIS; this is the geometric stand-in).  Ties in a coordinate go by element index, so the
+ * result is deterministic.  Errors: DGSWEM_EINVAL (null pointer, bad mesh indices, n_parts < 1 or
+ * above the element count). */
+DGSWEM_API int dgswem_partition_rcb(const dgswem_mesh *mesh, int32_t n_parts, int32_t *part);
+
+/* Sizes of part `rank`'s sub-mesh and exchange lists: nodes, elements (own + ghost layers 1 and 2),
+ * boundary-edge entries, peers (the other parts it exchanges with) and the total lengths of its
+ * send and receive lists. */
+typedef struct {
+  int32_t n_nodes, n_elems, n_bedges, n_own, n_ghost1, n_ghost2, n_peers, n_send, n_recv;
+} dgswem_part_counts;
+/* Errors: DGSWEM_EINVAL (null pointer, part entries or rank out of range, empty part),
+ * DGSWEM_EMESH (an edge shared by more than two elements, a boundary edge out of range). */
+DGSWEM_API int dgswem_part_sizes(const dgswem_mesh *mesh, const int32_t *part, int32_t n_parts, int32_t rank,
+                                 dgswem_part_counts *sizes);
+
+/* Caller-owned output arrays of dgswem_part_build, sized by dgswem_part_sizes.  The sub-mesh keeps
+ * the global element and node order: element i of the part is global element elem_global[i]
+ * (increasing), node j is global node node_global[j] (increasing), so a sub-mesh edge keeps its
+ * orientation.  elem_class[i]: 0 own, 1 first ghost layer (shares an edge with an own element),
+ * 2 second ghost layer.  bedge / bedge_type: the global boundary-edge entries of the part's
+ * elements.  For peer k (peer[k], increasing): send_count[k] own elements that are ghosts of that
+ * peer and recv_count[k] ghosts that it owns, concatenated over k in send_elems / recv_elems as
+ * part-local element indices, each group in increasing global index, so that this part's send
+ * group for q and q's receive group for this part list the same elements in the same order. */
+typedef struct {
+  double *xy;             /* [n_nodes][2] */
+  int32_t *tri;           /* [n_elems][3] */
+  int32_t *bedge;         /* [n_bedges][2] (may be NULL when n_bedges = 0) */
+  int32_t *bedge_type;    /* [n_bedges] */
+  double *bathy;          /* [n_nodes] */
+  int32_t *elem_global;   /* [n_elems] */
+  int32_t *elem_class;    /* [n_elems] */
+  int32_t *node_global;   /* [n_nodes] */
+  int32_t *peer, *send_count, *recv_count; /* [n_peers] */
+  int32_t *send_elems;    /* [n_send] */
+  int32_t *recv_elems;    /* [n_recv] */
+} dgswem_part_out;
+/* Fill the sub-mesh and exchange lists of part `rank` (errors as dgswem_part_sizes). */
+DGSWEM_API int dgswem_part_build(const dgswem_mesh *mesh, const double *bathy, const int32_t *part,
+                                 int32_t n_parts, int32_t rank, const dgswem_part_out *out);
 
 /* ---- allocation-free mass sums ----
  * The paper has no counterpart: this is a service for callers that may not allocate device
@@ -302,7 +392,8 @@ DGSWEM_API int dgswem_ensemble_set_fault(dgswem_ctx *ctx, int32_t skip_arrival);
  * process exits).  Larger n_elems is rejected with DGSWEM_ETOOBIG before any device work;
  * n_elems < 1 or a NULL pointer gives DGSWEM_EINVAL.  The first call on each device looks up the
  * buffer's device address (that device must be current), so make the first call before any
- * stream capture.  All calls share the buffer: calls that can overlap on the GPU (different
+ * stream capture.  The address is kept for the life of the process, which assumes that the
+ * device's primary context is not reset (cudaDeviceReset) or destroyed meanwhile.  All calls share the buffer: calls that can overlap on the GPU (different
  * streams, or different host threads) race and must be serialised by the caller.  Each call
  * overwrites every partial it reads, so no state carries over from a previous call. */
 #define DGSWEM_NOALLOC_MAX_ELEMS (1 << 26)

@@ -68,6 +68,13 @@ def _lib(omp: bool = False):
     lib.orc_destroy.argtypes = [C.c_void_p]
     lib.orc_sizes.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     lib.orc_step.argtypes = [C.c_void_p, C.c_int32]
+    lib.orc_stage.argtypes = [C.c_void_p]
+    lib.orc_stage.restype = C.c_int32
+    lib.orc_stage_count.argtypes = [C.c_void_p]
+    lib.orc_stage_count.restype = C.c_int32
+    lib.orc_get_register.argtypes = [C.c_void_p, C.c_int32, _dp, _dp, _dp]
+    lib.orc_set_register.argtypes = [C.c_void_p, C.c_int32, _dp, _dp, _dp]
+    lib.orc_set_flags.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
     lib.orc_get_state.argtypes = [C.c_void_p, _dp, _dp, _dp]
     lib.orc_set_state.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double]
     lib.orc_info.argtypes = [C.c_void_p, _dp, _dp, C.POINTER(C.c_int64)]
@@ -153,6 +160,26 @@ class Oracle:
 
     def step(self, n: int = 1):
         self.lib.orc_step(self.h, int(n))
+
+    def stage(self) -> int:
+        """Advance one stage of the time step in progress; returns the state buffer it wrote."""
+        return int(self.lib.orc_stage(self.h))
+
+    def stage_count(self) -> int:
+        return int(self.lib.orc_stage_count(self.h))
+
+    def register(self, r: int) -> np.ndarray:
+        out = np.empty((3, self.nd, self.ne))
+        self.lib.orc_get_register(self.h, int(r), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
+        return out
+
+    def set_register(self, r: int, u):
+        u = np.ascontiguousarray(u, np.float64)
+        self.lib.orc_set_register(self.h, int(r), _ptr(u[0]), _ptr(u[1]), _ptr(u[2]))
+
+    def set_flags(self, f):
+        f = np.ascontiguousarray(f, np.uint8)
+        self.lib.orc_set_flags(self.h, _ptr(f, C.c_uint8))
 
     def state(self) -> np.ndarray:
         out = np.empty((3, self.nd, self.ne))

@@ -117,6 +117,10 @@ typedef struct {
   double *MEAN;           /* scratch: element means used by the limiter */
   double dt, t0;
   int64_t nstep;
+  /* the time step in progress, one stage at a time (orc_stage): next stage index, the stage-time
+   * fraction tau and the register holding u^(i-1) */
+  int st_i, st_prev;
+  double st_tau;
   /* test-only manufactured-solution hooks */
   orc_field_cb mms_src, mms_bnd;
   int transmissive; /* test-only: every boundary ghost equals the interior trace */
@@ -954,26 +958,41 @@ static int rk_table(const orc_params *P, double a[8], double b[8], double c[8]) 
   return s;
 }
 
-/* one SSP-RK step: u^(0) = u^n, u^(i) = a_i u^n + b_i u^(i-1) + c_i dt L(u^(i-1)), limiter and
- * wet/dry after every stage, u^(n+1) = u^(s); buffers: 0 = u^n, 1 and 2 alternate */
-static void ssprk_step(orc *o) {
+/* one stage of the SSP-RK step in progress: u^(0) = u^n, u^(i) = a_i u^n + b_i u^(i-1) +
+ * c_i dt L(u^(i-1)), then limiter and wet/dry; u^(n+1) = u^(s).  Buffers: 0 = u^n, 1 and 2
+ * alternate, the last stage writes 0.  Returns the buffer written. */
+static int ssprk_stage(orc *o) {
   const double dt = o->dt;
   double a[8], b[8], c[8];
   const int s = rk_table(&o->prm, a, b, c);
   size_t n = (size_t)3 * o->nd * o->ne;
-  double tau = 0.0;
-  int prev = 0;
-  for (int i = 0; i < s; ++i) {
-    double ts = o->t0 + ((double)o->nstep + tau) * dt;
-    eval_L(o, prev, ts);
-    int out = (i == s - 1) ? 0 : (i % 2 == 0 ? 1 : 2);
-    double *U0 = o->U, *Up = o->U + (size_t)prev * n, *Uo = o->U + (size_t)out * n;
-    for (size_t k = 0; k < n; ++k) Uo[k] = a[i] * U0[k] + b[i] * Up[k] + c[i] * dt * o->RHS[k];
-    postprocess(o, out);
-    prev = out;
-    tau = b[i] * tau + c[i];
+  const int i = o->st_i;
+  if (i == 0) {
+    o->st_tau = 0.0;
+    o->st_prev = 0;
   }
-  o->nstep++;
+  const int prev = o->st_prev;
+  double ts = o->t0 + ((double)o->nstep + o->st_tau) * dt;
+  eval_L(o, prev, ts);
+  int out = (i == s - 1) ? 0 : (i % 2 == 0 ? 1 : 2);
+  double *U0 = o->U, *Up = o->U + (size_t)prev * n, *Uo = o->U + (size_t)out * n;
+  for (size_t k = 0; k < n; ++k) Uo[k] = a[i] * U0[k] + b[i] * Up[k] + c[i] * dt * o->RHS[k];
+  postprocess(o, out);
+  o->st_prev = out;
+  o->st_tau = b[i] * o->st_tau + c[i];
+  if (i == s - 1) {
+    o->st_i = 0;
+    o->nstep++;
+  } else {
+    o->st_i = i + 1;
+  }
+  return out;
+}
+
+static void ssprk_step(orc *o) {
+  double a[8], b[8], c[8];
+  const int s = rk_table(&o->prm, a, b, c);
+  for (int i = o->st_i; i < s; ++i) ssprk_stage(o);
 }
 
 /* ------------------------------------------------------------- time step */
@@ -1102,6 +1121,36 @@ void orc_step(orc *o, int32_t n) {
   for (int i = 0; i < n; ++i) ssprk_step(o);
 }
 
+/* The time step one stage at a time, for a domain split into parts (Sec. 5.3): each part advances
+ * its own and ghost elements by one stage, then the ghost elements' states and wet/dry flags are
+ * replaced by their owners' (orc_set_register, orc_set_flags) before the next stage.  orc_stage
+ * returns the state buffer the stage wrote (0 at the last stage, which completes the step). */
+int32_t orc_stage(orc *o) { return ssprk_stage(o); }
+
+int32_t orc_stage_count(const orc *o) {
+  double a[8], b[8], c[8];
+  return rk_table(&o->prm, a, b, c);
+}
+
+/* state buffer r (0 = u^n, 1 and 2 the stage buffers) as [3][nd][ne] arrays */
+void orc_get_register(const orc *o, int32_t r, double *ze, double *qx, double *qy) {
+  size_t m = (size_t)o->nd * o->ne, n = 3 * m;
+  const double *U = o->U + (size_t)r * n;
+  memcpy(ze, U, sizeof(double) * m);
+  memcpy(qx, U + m, sizeof(double) * m);
+  memcpy(qy, U + 2 * m, sizeof(double) * m);
+}
+
+void orc_set_register(orc *o, int32_t r, const double *ze, const double *qx, const double *qy) {
+  size_t m = (size_t)o->nd * o->ne, n = 3 * m;
+  double *U = o->U + (size_t)r * n;
+  memcpy(U, ze, sizeof(double) * m);
+  memcpy(U + m, qx, sizeof(double) * m);
+  memcpy(U + 2 * m, qy, sizeof(double) * m);
+}
+
+void orc_set_flags(orc *o, const unsigned char *f) { memcpy(o->WD, f, o->ne); }
+
 /* state as [3][nd][ne] arrays (zeta, qx, qy) in the caller's element order */
 void orc_get_state(const orc *o, double *ze, double *qx, double *qy) {
   size_t m = (size_t)o->nd * o->ne;
@@ -1117,6 +1166,7 @@ void orc_set_state(orc *o, const double *ze, const double *qx, const double *qy,
   memcpy(o->U + 2 * m, qy, sizeof(double) * m);
   o->t0 = t;
   o->nstep = 0;
+  o->st_i = 0;
 }
 
 void orc_info(const orc *o, double *dt, double *t, int64_t *steps) {

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgswem.so")
-SOURCES = ["api.cu", "mesh.cu", "common_kernels.cu", "kernels_f64.cu", "kernels_f32.cu", "ensemble.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "mesh.cu", "common_kernels.cu", "kernels_f64.cu", "kernels_f32.cu", "ensemble.cu", "noalloc.cu", "partition.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -179,6 +179,8 @@ void carve_mesh(Carver &k, const HostMesh &H, int p, bool mixed, DevMesh &m, int
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
   m.ne = ne;
   m.nn = nn;
+  m.nown = H.nown;
+  m.nact = H.nact;
   m.nint = nint;
   m.geo = k.take<char>(tsz * NGEO * ne);
   m.hbv = k.take<double>(3 * (size_t)ne);
@@ -199,6 +201,10 @@ void carve_mesh(Carver &k, const HostMesh &H, int p, bool mixed, DevMesh &m, int
   m.edhbq = mixed ? nullptr : k.take<char>(tsz * nqe_of(p) * nint);
   m.nodexy = k.take<double>(2 * (size_t)nn);
   m.elf = mixed ? k.take<float>(9 * (size_t)ne) : nullptr;
+  // the float form's double statics for the elements at the wetting/drying front
+  m.geo_d = mixed ? k.take<double>(NGEO * (size_t)ne) : nullptr;
+  m.lima_d = mixed ? k.take<double>(6 * (size_t)ne) : nullptr;
+  m.hbq_d = mixed ? k.take<double>((size_t)nqa_of(p) * ne) : nullptr;
   *perm = k.take<int>(ne);
   *iperm = k.take<int>(ne);
 }
@@ -214,6 +220,10 @@ static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
   c->U1 = k.take<double>(nu);
   c->U2 = c->nst >= 3 ? k.take<double>(nu) : nullptr;
   c->mean = k.take<char>(tsz * 3 * ne);
+  c->cls = k.take<uint8_t>(ne);
+  c->mean64 = c->mixed ? k.take<double>(3 * (size_t)ne) : nullptr;
+  c->flist = k.take<int>(ne);
+  c->fcnt = k.take<unsigned>(MAX_STAGES);
   c->wd = k.take<uint8_t>(ne);
   c->wd_stage = k.take<uint8_t>(ne);
   c->eflux = k.take<char>(tsz * 3 * NQE * nint);
@@ -275,11 +285,21 @@ static int prepare_tiles(dgswem_ctx *c, int tile) {
   return 0;
 }
 
+// The mesh view whose every element counts as own and updated: the initial and single-operator
+// wet/dry and limiter calls apply to the ghost elements of a part as well.
+static DevMesh whole(const DevMesh &m) {
+  DevMesh a = m;
+  a.nown = a.nact = a.ne;
+  return a;
+}
+
 // ------------------------------------------------------------------ one step
 static const char *kname_forcing = "forcing";
 static const char *kname_edge = "edge_flux";
 static const char *kname_element = "element_update";
 static const char *kname_limwd = "limiter_wetdry";
+static const char *kname_front = "front_update";
+static const char *kname_limwd_front = "front_limiter_wetdry";
 static const char *kname_advance = "advance";
 
 static void mark(dgswem_ctx *c, const char *name, std::vector<const char *> *names, int *ev_i) {
@@ -323,6 +343,15 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
     sa.rcdt = sa.rc * c->dt;
     sa.rk_form = rk_form_of(sa.ra, sa.rb, sa.rc);
     sa.err = c->err;
+    // float form with wetting/drying: the element kernels list the front elements, which the front
+    // kernels update in double
+    const bool front = c->mixed && ph.wetdry;
+    sa.cls = front ? c->cls : nullptr;
+    sa.mean64 = front ? c->mean64 : nullptr;
+    sa.flist = c->flist;
+    sa.fcnt = c->fcnt + stage;
+    sa.fcnt_prev = front ? c->fcnt + (stage + c->nst - 1) % c->nst : nullptr;
+    sa.fbase = 0;
     if (variant == DGSWEM_VARIANT_TILED || variant == DGSWEM_VARIANT_TILED_WIDE) {
       mark(c, kname_element, names, &ev_i);
       launch_tile(c->mixed, c->P, variant == DGSWEM_VARIANT_TILED_WIDE, false, c->dm, c->tiles, sa, ph, cfg);
@@ -334,9 +363,18 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
       mark(c, kname_element, names, &ev_i);
       launch_element(c->mixed, c->P, split, false, c->dm, sa, ph, cfg);
     }
+    if (front) {
+      mark(c, kname_front, names, &ev_i);
+      launch_front(c->P, c->dm, sa, ph, 0, c->st);
+    }
     if (ph.limiter || ph.wetdry) {
+      if (front) {  // before the float limiter, which changes the non-front states they read
+        mark(c, kname_limwd_front, names, &ev_i);
+        launch_limwd_front(c->P, ph.limiter, ph.wetdry, c->dm, out, c->mean64, c->cls, c->wd, ph, c->err, c->flist,
+                           sa.fcnt, c->st);
+      }
       mark(c, kname_limwd, names, &ev_i);
-      launch_limwd(c->mixed, c->P, ph.limiter, ph.wetdry, c->dm, out, c->mean, c->wd, ph, c->err, cfg);
+      launch_limwd(c->mixed, c->P, ph.limiter, ph.wetdry, c->dm, out, c->mean, c->wd, ph, c->err, cfg, sa.cls);
     }
   }
   mark(c, kname_advance, names, &ev_i);
@@ -349,7 +387,7 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
 
 static int kernels_in_step(const dgswem_ctx *c, int variant) {
   const int per_stage = 1 + ((c->ph.hurricane && !c->mixed) ? 1 : 0) + ((variant == DGSWEM_VARIANT_SPLIT && c->dm.nint > 0) ? 1 : 0) +
-                  ((c->ph.limiter || c->ph.wetdry) ? 1 : 0);
+                  ((c->ph.limiter || c->ph.wetdry) ? 1 : 0) + ((c->mixed && c->ph.wetdry) ? 2 : 0);
   return c->nst * per_stage + 1;
 }
 
@@ -448,9 +486,11 @@ int upload_mesh(dgswem_ctx *c, const HostMesh &H, const DevMesh &m, int *perm, i
     std::vector<double> v;
     area_point_hb(c->P, H, v);
     c->host_keep.push_back(typed(v, c->mixed));
+    if (m.hbq_d) c->host_keep.push_back(typed(v, false));
     edge_point_hb(c->P, H.edhb.data(), H.edhb.data() + H.nint, H.nint, v);
     c->host_keep.push_back(typed(v, c->mixed));
   }
+  const size_t ihbq = base + 3, iedhbq = base + (m.hbq_d ? 5 : 4);
   int r = 0;
   r |= put(m.geo, c->host_keep[base].data(), c->host_keep[base].size());
   r |= put(m.hbv, H.hbv.data(), H.hbv.size() * sizeof(double));
@@ -466,8 +506,11 @@ int upload_mesh(dgswem_ctx *c, const HostMesh &H, const DevMesh &m, int *perm, i
   r |= put(m.edle, H.edle.data(), H.edle.size());
   r |= put(m.edgeo, c->host_keep[base + 2].data(), c->host_keep[base + 2].size());
   r |= put(m.edhb, H.edhb.data(), H.edhb.size() * sizeof(double));
-  if (m.hbq) r |= put(m.hbq, c->host_keep[base + 3].data(), c->host_keep[base + 3].size());
-  if (m.edhbq) r |= put(m.edhbq, c->host_keep[base + 4].data(), c->host_keep[base + 4].size());
+  if (m.hbq) r |= put(m.hbq, c->host_keep[ihbq].data(), c->host_keep[ihbq].size());
+  if (m.edhbq) r |= put(m.edhbq, c->host_keep[iedhbq].data(), c->host_keep[iedhbq].size());
+  if (m.geo_d) r |= put(m.geo_d, H.geo.data(), H.geo.size() * sizeof(double));
+  if (m.lima_d) r |= put(m.lima_d, H.lima.data(), H.lima.size() * sizeof(double));
+  if (m.hbq_d) r |= put(m.hbq_d, c->host_keep[base + 4].data(), c->host_keep[base + 4].size());
   r |= put(m.nodexy, H.nodexy.data(), H.nodexy.size() * sizeof(double));
   if (m.elf) {
     c->host_keep.push_back(element_floats(H));
@@ -584,6 +627,7 @@ static int autotune(dgswem_ctx *c, int *best_variant, int *best_block) {
     cudaMemcpyAsync(c->wd, save_wd.data(), c->hm.ne, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(c->step, 0, sizeof(long long), s);
     cudaMemsetAsync(c->err, 0, sizeof(int), s);
+    cudaMemsetAsync(c->fcnt, 0, MAX_STAGES * sizeof(unsigned), s);
   };
   float best = INFINITY;
   bool warmed = false;
@@ -629,6 +673,7 @@ int dgswem_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream) 
   cudaMemsetAsync(c->step, 0, sizeof(long long), s);
   cudaMemsetAsync(c->err, 0, sizeof(int), s);
   cudaMemsetAsync(c->wd, 0, c->hm.ne, s);
+  cudaMemsetAsync(c->fcnt, 0, MAX_STAGES * sizeof(unsigned), s);
   cudaMemsetAsync(c->U1, 0, nu * sizeof(double), s);
   if (c->init_kind == 1) {
     cudaMemcpyAsync(c->U0, c->init_modal.data(), nu * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -639,7 +684,7 @@ int dgswem_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream) 
     cudaMemsetAsync(c->U0, 0, nu * sizeof(double), s);
   }
   const LaunchCfg cfg{128, s};
-  if (c->ph.wetdry) launch_limwd(c->mixed, c->P, false, 1, c->dm, c->U0, c->mean, c->wd, c->ph, c->err, cfg);
+  if (c->ph.wetdry) launch_limwd(c->mixed, c->P, false, 1, whole(c->dm), c->U0, c->mean, c->wd, c->ph, c->err, cfg);
   if (c->prm.dt > 0) {
     c->dt = c->prm.dt;
   } else {
@@ -714,7 +759,7 @@ int dgswem_set_state(dgswem_ctx *c, const double *hz, const double *hqx, const d
   c->t0 = t;
   c->steps_done = 0;
   if (c->ph.wetdry)  // recompute the flags only; the state is not modified
-    launch_limwd(c->mixed, c->P, false, 2, c->dm, c->U0, c->mean, c->wd, c->ph, c->err, LaunchCfg{128, c->st});
+    launch_limwd(c->mixed, c->P, false, 2, whole(c->dm), c->U0, c->mean, c->wd, c->ph, c->err, LaunchCfg{128, c->st});
   if (int r = ctx_cuda(c, cudaGetLastError(), "set_state")) return r;
   // the captured graph bakes t0 into its kernel parameters: recapture
   return capture_graph(c, c->variant, c->block, c->timing);
@@ -798,12 +843,25 @@ int dgswem_eval_rhs(dgswem_ctx *c, double t, double *h_out) {
   sa.rk_form = 0;
   sa.err = c->err;
   sa.tide_t = t;
+  // float form with wetting/drying: the front elements take the double path, as in a step
+  const bool front = c->mixed && c->ph.wetdry;
+  sa.cls = front ? c->cls : nullptr;
+  sa.mean64 = nullptr;
+  sa.flist = c->flist;
+  sa.fcnt = c->fcnt;
+  sa.fcnt_prev = nullptr;
+  sa.fbase = 0;
+  if (front) cudaMemsetAsync(c->fcnt, 0, sizeof(unsigned), c->st);
   const bool split = c->variant == DGSWEM_VARIANT_SPLIT;
   if (c->variant == DGSWEM_VARIANT_TILED || c->variant == DGSWEM_VARIANT_TILED_WIDE) {
     launch_tile(c->mixed, c->P, c->variant == DGSWEM_VARIANT_TILED_WIDE, true, c->dm, c->tiles, sa, c->ph, cfg);
   } else {
     if (split) launch_edge(c->mixed, c->P, c->dm, sa, c->ph, cfg);
     launch_element(c->mixed, c->P, split, true, c->dm, sa, c->ph, cfg);
+  }
+  if (front) {
+    launch_front(c->P, c->dm, sa, c->ph, 1, c->st);
+    cudaMemsetAsync(c->fcnt, 0, sizeof(unsigned), c->st);  // the step graph expects zero counters
   }
   const int ne = c->hm.ne, ND = c->ND;
   launch_permute(c->U1, c->staging, c->d_iperm, 3 * ND, ne, c->st);
@@ -819,7 +877,7 @@ int dgswem_apply_limiter(dgswem_ctx *c) {
   if (c->sticky) return c->sticky;
   if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
   launch_copy_means(c->mixed, c->P, c->hm.ne, c->U0, c->mean, c->st);
-  launch_limwd(c->mixed, c->P, true, 0, c->dm, c->U0, c->mean, c->wd, c->ph, c->err, LaunchCfg{c->block, c->st});
+  launch_limwd(c->mixed, c->P, true, 0, whole(c->dm), c->U0, c->mean, c->wd, c->ph, c->err, LaunchCfg{c->block, c->st});
   if (int r = ctx_cuda(c, cudaGetLastError(), "limiter")) return r;
   return read_error_word(c);
 }
@@ -831,7 +889,7 @@ int dgswem_apply_wetdry(dgswem_ctx *c) {
   if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
   Phys ph = c->ph;
   if (!(ph.h0 > 0)) return ctx_fail(c, DGSWEM_EINVAL, "wetting/drying is off (h0 = 0)");
-  launch_limwd(c->mixed, c->P, false, 1, c->dm, c->U0, c->mean, c->wd, ph, c->err, LaunchCfg{c->block, c->st});
+  launch_limwd(c->mixed, c->P, false, 1, whole(c->dm), c->U0, c->mean, c->wd, ph, c->err, LaunchCfg{c->block, c->st});
   if (int r = ctx_cuda(c, cudaGetLastError(), "wetdry")) return r;
   return read_error_word(c);
 }

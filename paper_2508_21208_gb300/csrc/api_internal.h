@@ -52,6 +52,10 @@ struct dgswem_ctx {
   int *d_perm = nullptr, *d_iperm = nullptr;
   double *U0 = nullptr, *U1 = nullptr, *U2 = nullptr, *partial = nullptr, *result = nullptr, *staging = nullptr;
   void *mean = nullptr;  // T [3][ne] element means for the limiter
+  uint8_t *cls = nullptr;     // [ne] wetting/drying front class (float form)
+  double *mean64 = nullptr;   // [3][ne] the front elements' means in double (float form)
+  int *flist = nullptr;       // [ne] front list (float form)
+  unsigned *fcnt = nullptr;   // [MAX_STAGES] front list counters, one per stage
   uint8_t *wd = nullptr, *wd_stage = nullptr, *emode = nullptr;
   void *eflux = nullptr, *frc = nullptr;
   long long *step = nullptr;

@@ -2,6 +2,7 @@
 // means, the CFL time step, the compensated mass sum, element reordering and the step counter.
 #include <cstdint>
 
+#include "compsum.cuh"
 #include "internal.h"
 
 namespace dg {
@@ -75,21 +76,7 @@ void launch_dt(int p, const DevMesh &m, const double *u, const Phys &ph, unsigne
     k_dt<2><<<nblk(m.ne, 256), 256, 0, s>>>(m, u, ph.g, ph.h0, best);
 }
 
-// ---- compensated sums: Neumaier within a thread, TwoSum when combining, fixed order.
-struct Comp {
-  double s, c;
-};
-__device__ __forceinline__ void comp_add(Comp &a, double x) {
-  const double t = a.s + x;
-  a.c += fabs(a.s) >= fabs(x) ? (a.s - t) + x : (x - t) + a.s;
-  a.s = t;
-}
-__device__ __forceinline__ Comp comp_merge(Comp a, Comp b) {
-  comp_add(a, b.s);
-  a.c += b.c;
-  return a;
-}
-
+// ---- compensated sums (compsum.cuh), fixed order.
 constexpr int MASS_THREADS = 256;
 constexpr int MASS_PER_BLOCK = MASS_THREADS * 8;
 
@@ -103,28 +90,18 @@ __global__ void __launch_bounds__(MASS_THREADS) k_mass_partial(const DevMesh m, 
   const int base = blockIdx.x * MASS_PER_BLOCK;
   for (int i = threadIdx.x; i < MASS_PER_BLOCK; i += MASS_THREADS) {
     const int e = base + i;
-    if (e >= ne) break;
+    if (e >= m.nown) break;
     const double z = u[e], ar = m.area[e];
     const double hm = (m.hbv[e] + m.hbv[ne + e] + m.hbv[2 * (size_t)ne + e]) / 3.0;
     comp_add(a, ar * z);
     comp_add(b, ar * (z + hm));
   }
-  __shared__ Comp sa[MASS_THREADS], sb[MASS_THREADS];
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  __syncthreads();
-  for (int w = MASS_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      sa[threadIdx.x] = comp_merge(sa[threadIdx.x], sa[threadIdx.x + w]);
-      sb[threadIdx.x] = comp_merge(sb[threadIdx.x], sb[threadIdx.x + w]);
-    }
-    __syncthreads();
-  }
+  comp_block_reduce<MASS_THREADS>(a, b);
   if (threadIdx.x == 0) {
-    partial[4 * blockIdx.x + 0] = sa[0].s;
-    partial[4 * blockIdx.x + 1] = sa[0].c;
-    partial[4 * blockIdx.x + 2] = sb[0].s;
-    partial[4 * blockIdx.x + 3] = sb[0].c;
+    partial[4 * blockIdx.x + 0] = a.s;
+    partial[4 * blockIdx.x + 1] = a.c;
+    partial[4 * blockIdx.x + 2] = b.s;
+    partial[4 * blockIdx.x + 3] = b.c;
   }
 }
 
@@ -134,26 +111,16 @@ __global__ void __launch_bounds__(MASS_THREADS) k_mass_final(int nb, const doubl
     a = comp_merge(a, Comp{partial[4 * i], partial[4 * i + 1]});
     b = comp_merge(b, Comp{partial[4 * i + 2], partial[4 * i + 3]});
   }
-  __shared__ Comp sa[MASS_THREADS], sb[MASS_THREADS];
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  __syncthreads();
-  for (int w = MASS_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      sa[threadIdx.x] = comp_merge(sa[threadIdx.x], sa[threadIdx.x + w]);
-      sb[threadIdx.x] = comp_merge(sb[threadIdx.x], sb[threadIdx.x + w]);
-    }
-    __syncthreads();
-  }
+  comp_block_reduce<MASS_THREADS>(a, b);
   if (threadIdx.x == 0) {
-    result[0] = sa[0].s + sa[0].c;
-    result[1] = sb[0].s + sb[0].c;
+    result[0] = a.s + a.c;
+    result[1] = b.s + b.c;
   }
 }
 
 void launch_mass(int p, const DevMesh &m, const double *u, double *partial, double *result, cudaStream_t s) {
   (void)p;
-  const int nb = mass_partial_count(m.ne);
+  const int nb = mass_partial_count(m.nown);  // a part sums its own elements
   k_mass_partial<<<nb, MASS_THREADS, 0, s>>>(m, u, partial);
   k_mass_final<<<1, MASS_THREADS, 0, s>>>(nb, partial, result);
 }

@@ -24,6 +24,8 @@ struct EnsMember {
   double t0 = 0.0, dt = 0.0;
   double *U0 = nullptr, *U1 = nullptr, *U2 = nullptr;
   void *mean = nullptr;  // T [3][ne]
+  uint8_t *cls = nullptr;    // [ne] wetting/drying front class (float form)
+  double *mean64 = nullptr;  // [3][ne] the front elements' means in double (float form)
   uint8_t *wd = nullptr;
   void *frc = nullptr;
 };
@@ -49,7 +51,9 @@ struct EnsembleState {
   std::vector<int> h_etile, h_ntile;
   std::vector<MemberDev> h_mem;
   bool persistent = true;
-  int block = 128, grid = 0, fault = 0, any_limwd = 0, any_inline = 0;
+  int block = 128, grid = 0, fault = 0, any_limwd = 0, any_inline = 0, any_front = 0;
+  int *flist = nullptr;       // front list of all members (float form with wetting/drying)
+  unsigned *fcnt = nullptr;   // its counter per stage
   unsigned long long timeout_ns = 1000000000ull;  // 1 s per grid-barrier wait
   std::vector<TuneEntry> tune;
 };
@@ -78,10 +82,16 @@ static void ens_layout(dgswem_ctx *c, char *base, size_t *bytes) {
     mb.U1 = k.take<double>(nu);
     mb.U2 = c->nst >= 3 ? k.take<double>(nu) : nullptr;
     mb.mean = k.take<char>(tsz * 3 * (size_t)H.ne);
+    mb.cls = k.take<uint8_t>(H.ne);
+    mb.mean64 = c->mixed ? k.take<double>(3 * (size_t)H.ne) : nullptr;
     mb.wd = k.take<uint8_t>(H.ne);
     mb.frc = k.take<char>(tsz * 3 * H.nn);
     stage = std::max(stage, std::max(nu, 3 * (size_t)H.nn));
   }
+  size_t ne_all = 0;
+  for (EnsMember &mb : E.mem) ne_all += E.meshes[mb.mesh].hm.ne;
+  E.flist = k.take<int>(ne_all);
+  E.fcnt = k.take<unsigned>(MAX_STAGES);
   E.d_mem = k.take<MemberDev>(E.mem.size());
   E.d_etile = k.take<int>(E.max_etile);
   E.d_ntile = k.take<int>(E.max_ntile);
@@ -102,6 +112,7 @@ static void build_tiles(dgswem_ctx *c, int block) {
   E.h_mem.assign(E.mem.size(), MemberDev{});
   E.any_limwd = 0;
   E.any_inline = 0;
+  E.any_front = 0;
   for (size_t i = 0; i < E.mem.size(); ++i) {
     EnsMember &mb = E.mem[i];
     const EnsMesh &M = E.meshes[mb.mesh];
@@ -115,6 +126,10 @@ static void build_tiles(dgswem_ctx *c, int block) {
     d.mean = mb.mean;
     d.wd = mb.wd;
     d.frc = mb.frc;
+    // float form with wetting/drying: the front elements take the double path
+    d.cls = (c->mixed && mb.ph.wetdry) ? mb.cls : nullptr;
+    d.mean64 = d.cls ? mb.mean64 : nullptr;
+    E.any_front |= d.cls ? 1 : 0;
     d.t0 = mb.t0;
     d.dt = mb.dt;
     d.etile0 = (int)E.h_etile.size();
@@ -174,6 +189,7 @@ static int init_states(dgswem_ctx *c) {
   }
   cudaMemsetAsync(c->step, 0, sizeof(long long), s);
   cudaMemsetAsync(E.bar, 0, 2 * sizeof(unsigned), s);
+  cudaMemsetAsync(E.fcnt, 0, MAX_STAGES * sizeof(unsigned), s);
   if (int r = ctx_cuda(c, cudaStreamSynchronize(s), "ensemble init")) return r;
   return ctx_cuda(c, cudaGetLastError(), "ensemble init");
 }
@@ -208,6 +224,9 @@ void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names) {
   a.fault = E.fault;
   a.any_limwd = E.any_limwd;
   a.any_inline = E.any_inline;
+  a.any_front = E.any_front;
+  a.flist = E.flist;
+  a.fcnt = E.fcnt;
   a.timeout_ns = E.timeout_ns;
   if (names) {
     cudaEventRecordWithFlags(c->ev[0], c->st, cudaEventRecordExternal);
@@ -217,7 +236,7 @@ void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names) {
   if (e != cudaSuccess) ctx_cuda(c, e, "ensemble launch");
   if (!E.persistent) launch_advance(c->step, c->st);
   if (names) cudaEventRecordWithFlags(c->ev[1], c->st, cudaEventRecordExternal);
-  c->kernels_per_step = E.persistent ? 1 : c->nst * ((E.n_ntile > 0) + 1 + E.any_limwd) + 1;
+  c->kernels_per_step = E.persistent ? 1 : c->nst * ((E.n_ntile > 0) + 1 + E.any_limwd + 2 * E.any_front) + 1;
 }
 
 static int upload_mesh_tiles(dgswem_ctx *c, EnsMesh &M, int tile) {
@@ -461,6 +480,21 @@ int dgswem_ensemble_get_state(dgswem_ctx *c, int32_t member, double *hz, double 
       if (int r = ctx_cuda(c, cudaMemcpyAsync(dst[v], c->staging + (size_t)v * ND * ne, (size_t)ND * ne * sizeof(double),
                                               cudaMemcpyDeviceToHost, c->st), "member readback"))
         return r;
+  return read_error_word(c);
+}
+
+int dgswem_ensemble_get_flags(dgswem_ctx *c, int32_t member, uint8_t *h) {
+  if (!c || !c->ensemble || !h) return DGSWEM_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
+  EnsembleState &E = *c->ens;
+  if (member < 0 || member >= (int)E.mem.size()) return DGSWEM_EINVAL;
+  const EnsMember &mb = E.mem[member];
+  const EnsMesh &M = E.meshes[mb.mesh];
+  uint8_t *stage = reinterpret_cast<uint8_t *>(c->staging);  // at least ne bytes
+  launch_permute_u8(mb.wd, stage, M.iperm, M.hm.ne, c->st);
+  if (int r = ctx_cuda(c, cudaMemcpyAsync(h, stage, M.hm.ne, cudaMemcpyDeviceToHost, c->st), "member flags readback"))
+    return r;
   return read_error_word(c);
 }
 

@@ -35,6 +35,10 @@ constexpr int NBR_RIVER = -3;
 // Mesh after preprocessing, elements in internal (locality) order.
 struct HostMesh {
   int ne = 0, nn = 0, nint = 0, nbnd = 0;
+  // part of a partitioned domain (Sec. 5.3): elements [0, nown) are this part's own, [nown, nact)
+  // the first ghost layer (updated here too, redundantly), [nact, ne) the second ghost layer (read
+  // only); without a partition nown = nact = ne
+  int nown = 0, nact = 0;
   std::vector<int> perm;          // internal index -> caller index
   std::vector<int> iperm;         // caller index -> internal index
   std::vector<int> vnode;         // [3][ne] node ids
@@ -69,9 +73,11 @@ struct TileEdges {
 void build_tile_edges(const HostMesh &H, int tile, TileEdges &out);
 inline int max_tile_edges(const HostMesh &H) { return 2 * H.nint + H.nbnd; }
 
-// Returns 0 or DGSWEM_EMESH / DGSWEM_EINVAL with a message.
+// Returns 0 or DGSWEM_EMESH / DGSWEM_EINVAL with a message.  elem_class (optional, caller order):
+// 0 own, 1 first ghost layer, 2 second ghost layer; the internal order then puts the classes in
+// that order (Hilbert order within each).
 int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, HostMesh &out,
-                    std::string &msg);
+                    std::string &msg, const int32_t *elem_class = nullptr);
 
 // ------------------------------------------------------------------ device-side views
 // Float copies of the constants the float form uses, rounded once on the host (a double -> float
@@ -104,6 +110,7 @@ inline int rk_form_of(double a, double b, double c) {
 
 struct DevMesh {
   int ne, nn, nint;
+  int nown, nact;          // partitioned domain: own / updated element counts (HostMesh); else ne
   const void *geo;         // T [NGEO][ne]
   const double *hbv;       // [3][ne]
   const double *area;      // [ne]
@@ -123,6 +130,9 @@ struct DevMesh {
   const double *nodexy;    // [2][nn]
   const float *elf;        // float form: [9][ne] vertex h_b (3), vertex x (3), vertex y (3), rounded
                            // once on the host like the kernels' double -> float conversion
+  // float form only: double copies of geo ([NGEO][ne]), lima ([6][ne]) and hbq ([NQA][ne]) for
+  // the elements at the wetting/drying front, whose update runs in double (null in the FP64 form)
+  const double *geo_d, *lima_d, *hbq_d;
 };
 
 
@@ -154,6 +164,16 @@ struct StageArgs {
   int rk_form;             // rk_form_of(ra, rb, rc)
   int *err;
   double tide_t;           // stage time when clk.step is null (single operator calls)
+  // Float form with wetting/drying (null otherwise): the element kernels mark each element at the
+  // wetting/drying front with cls[e] = 1 (0 elsewhere), skip it, and append its flat index
+  // fbase + e to flist, counting in *fcnt; the front kernels then update the listed elements in
+  // double and write their means in double to mean64.  *fcnt_prev, the previous stage's counter,
+  // is reset by the element kernels (its readers have finished).
+  uint8_t *cls;
+  double *mean64;
+  int *flist;
+  unsigned *fcnt, *fcnt_prev;
+  int fbase;
 };
 
 struct DevTiles {
@@ -176,6 +196,8 @@ struct MemberDev {
   void *mean;              // T [3][ne] element means for the limiter
   uint8_t *wd;
   void *frc;               // T [3][nn]
+  uint8_t *cls;            // float form with wetting/drying: front class per element (StageArgs)
+  double *mean64;          // float form with wetting/drying: the front elements' means in double
   double t0, dt;           // stage time = t0 + (step + stage) * dt (its own dt)
   int etile0, ntile0;      // first element / node tile of this member in the flat tile lists
 };
@@ -194,6 +216,9 @@ struct EnsArgs {
   int fault;               // test hook: the last block never arrives at a barrier
   int any_limwd;
   int any_inline;          // some member evaluates the vortex inline (float form): tile_smem_bytes(, true)
+  int any_front;           // some member has front elements to list (float form with wetting/drying)
+  int *flist;              // the front list of every member (flat element indices: tile * block + i)
+  unsigned *fcnt;          // its counter per stage
   unsigned long long timeout_ns;
 };
 
@@ -244,7 +269,7 @@ struct LaunchCfg {
                             const StageArgs &s, const Phys &ph, const LaunchCfg &c);             \
   void launch_limwd_##SUF(int p, bool do_lim, int do_wd, const DevMesh &m, double *u,            \
                           const void *mean, uint8_t *wd, const Phys &ph, int *err,               \
-                          const LaunchCfg &c);                                                   \
+                          const LaunchCfg &c, const uint8_t *cls);                              \
   void launch_tile_##SUF(int p, bool wide, bool write_rhs, const DevMesh &m, const DevTiles &tl,   \
                          const StageArgs &s, const Phys &ph, const LaunchCfg &c);                 \
   void prepare_tile_##SUF();                                                                      \
@@ -270,12 +295,20 @@ inline void launch_element(bool mixed, int p, bool split, bool write_rhs, const 
   mixed ? launch_element_f32(p, split, write_rhs, m, s, ph, c)
         : launch_element_f64(p, split, write_rhs, m, s, ph, c);
 }
+// cls (float form only): elements with cls[e] = 1 are skipped (the front kernels handle them);
+// null: every element.
 inline void launch_limwd(bool mixed, int p, bool do_lim, int do_wd, const DevMesh &m, double *u,
                          const void *mean, uint8_t *wd, const Phys &ph, int *err,
-                         const LaunchCfg &c) {
-  mixed ? launch_limwd_f32(p, do_lim, do_wd, m, u, mean, wd, ph, err, c)
-        : launch_limwd_f64(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
+                         const LaunchCfg &c, const uint8_t *cls = nullptr) {
+  mixed ? launch_limwd_f32(p, do_lim, do_wd, m, u, mean, wd, ph, err, c, cls)
+        : launch_limwd_f64(p, do_lim, do_wd, m, u, mean, wd, ph, err, c, nullptr);
 }
+// Float form with wetting/drying: the double update of the listed front elements (s.flist,
+// *s.fcnt), then their double limiter and wet/dry.  kernels_f32.cu.
+void launch_front(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, int write_rhs, cudaStream_t st);
+void launch_limwd_front(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean64,
+                        const uint8_t *cls, uint8_t *wd, const Phys &ph, int *err, const int *flist,
+                        const unsigned *fcnt, cudaStream_t st);
 inline void launch_tile(bool mixed, int p, bool wide, bool write_rhs, const DevMesh &m, const DevTiles &tl,
                         const StageArgs &s, const Phys &ph, const LaunchCfg &c) {
   mixed ? launch_tile_f32(p, wide, write_rhs, m, tl, s, ph, c) : launch_tile_f64(p, wide, write_rhs, m, tl, s, ph, c);

@@ -3,6 +3,7 @@
 // Included by kernels_f64.cu (T = double: the FP64 form) and kernels_f32.cu (T = float: the
 // mixed form, where the RK state, the RK update and all wet/dry depth tests stay in double).
 #pragma once
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -634,11 +635,12 @@ __device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph
 
 }
 
-// Inverse mass matrix, closed-form linear sources and the RK stage; writes u^(s+1) and the means.
+// Inverse mass matrix, closed-form linear sources and the RK stage; writes u^(s+1) and the means
+// (the limiter's copy in MT, the form's type; the double path also writes them to s.mean64 when set).
 // ctr: the storm centre at the stage time (once per block), or null; vxy: the element's vertex
 // coordinates already in T (x0, x1, x2 at vxy[0], vxy[vs], vxy[2 vs], then y), or null to read the
 // nodes.
-template <int P, typename T>
+template <int P, typename T, typename MT = T>
 __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s, const Phys &ph,
                                             const int write_rhs, const int e, const ElemCtx<P, T> &c,
                                             T r[3][nd_of(P)], const double *ctr = nullptr,
@@ -756,19 +758,80 @@ __device__ __forceinline__ void elem_finish(const DevMesh &m, const StageArgs &s
       }
       bad |= !finite_bits(out);
       s.uout[ix] = out;
-      if (k == 0 && s.mean) static_cast<T *>(s.mean)[(size_t)v * ne + e] = from_d<T>(out);
+      if (k == 0) {
+        if (s.mean) static_cast<MT *>(s.mean)[(size_t)v * ne + e] = from_d<MT>(out);
+        if constexpr (sizeof(T) == sizeof(double))
+          if (s.mean64) s.mean64[(size_t)v * ne + e] = out;
+      }
     }
   }
   if (bad) atomicOr(s.err, ERR_NONFINITE);
 }
 
-template <int P, typename T, bool SPLIT>
+// ------------------------------------------------------------------------ wetting/drying front
+// Float form with wetting/drying.  Near the shoreline the vertex depths sit within a float rounding
+// of the dry threshold h0 (a surface elevation of metres carries a float ulp of ~1e-7 m, against
+// the 1e-10 m tolerance of the depth tests), so a float evaluation there flips wet/dry decisions
+// that the FP64 arithmetic takes the other way.  The elements at the wetting/drying front are
+// therefore updated in double, from double statics (DevMesh geo_d / lima_d / hbq_d), with the same
+// operations as the FP64 form: area, edge and source arithmetic, limiter and wet/dry.  An element
+// is at the front, given the flags at the start of the stage, if it is
+//  - partially wet;
+//  - wet, with a face neighbour that is not wet;
+//  - dry, with a face neighbour that is not dry, an open-ocean or river edge, or rain falling.
+// A dry element whose neighbours are all dry is left to the float path: walls on every edge and no
+// momentum keep its surface exactly unchanged in either arithmetic (and wet/dry then removes the
+// float momentum and restores the flat depth).  The element kernels list the front elements, and
+// two small kernels spread over all SMs update them (k_front) and limit them (k_limwd_front).
+constexpr uint8_t NBC_LAND = 255;  // neighbour code across a land edge
+constexpr uint8_t NBC_OPEN = 254;  // across an open-ocean or river edge
+
+// fe: the element's flag; n0..n2: its neighbours' flags (0 wet, 1 partially wet, 2 dry) or NBC_*.
+__device__ __forceinline__ bool is_front(uint8_t fe, uint8_t n0, uint8_t n1, uint8_t n2, bool rain) {
+  if (fe == 1) return true;
+  if (fe == 0) return (n0 == 1 || n0 == 2) || (n1 == 1 || n1 == 2) || (n2 == 1 || n2 == 2);
+  return rain || (n0 != 2 && n0 != NBC_LAND) || (n1 != 2 && n1 != NBC_LAND) || (n2 != 2 && n2 != NBC_LAND);
+}
+
+// Append flat index id to the front list (called only by the threads whose element is at the
+// front): one atomic per group of converged threads.
+__device__ __forceinline__ void front_append(const StageArgs &s, int id) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(s.fcnt, (unsigned)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  s.flist[base + __popc(mask & ((1u << lane) - 1u))] = id;
+}
+
+// The element kernels of a stage reset the previous stage's list counter (all its readers ran).
+__device__ __forceinline__ void front_reset_prev(const StageArgs &s) {
+  if (s.fcnt_prev && blockIdx.x == 0 && threadIdx.x == 0) *s.fcnt_prev = 0u;
+}
+
+template <int P, typename T, bool SPLIT, typename MT = T>
 __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &s, const Phys &ph,
                                              const int write_rhs, const int e,
                                              const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
   constexpr int ND = nd_of(P), NQE = nqe_of(P);
   const Tab<T> &tb = ctab<T>(P);
   const int ne = m.ne;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (s.cls) {  // s.cls implies s.wd; the front elements are left to k_front
+      uint8_t nf[3];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const int j = m.nbr[(size_t)l * ne + e];
+        nf[l] = j >= 0 ? s.wd[j] : (j == NBR_LAND ? NBC_LAND : NBC_OPEN);
+      }
+      const bool front = is_front(s.wd[e], nf[0], nf[1], nf[2], ph.rain != 0.0);
+      s.cls[e] = front ? 1 : 0;
+      if (front) {
+        front_append(s, s.fbase + e);
+        return;
+      }
+    }
+  }
   const T g = pc<T>(ph.g, ph.f.g), sqg = pc<T>(ph.sqrt_g, ph.f.sqrt_g);
   ElemCtx<P, T> c;
   elem_load<P, T>(m, s.uin, e, c);
@@ -867,17 +930,55 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
     }
   }
 
-  elem_finish<P, T>(m, s, ph, write_rhs, e, c, r);
+  elem_finish<P, T, MT>(m, s, ph, write_rhs, e, c, r);
 }
 
+template <int P>
+__device__ __forceinline__ void front_update_body(const DevMesh &m, const StageArgs &s, const Phys &ph,
+                                                  int write_rhs, int e) {
+  constexpr int ND = nd_of(P), NQE = nqe_of(P);
+  DevMesh md = m;
+  md.geo = m.geo_d;
+  md.lima = m.lima_d;
+  md.hbq = m.hbq_d;
+  StageArgs sd = s;
+  sd.cls = nullptr;
+  double phe[3][NQE][ND];
+  const Tab<double> &td = c_td[P - 1];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int q = 0; q < NQE; ++q)
+#pragma unroll
+      for (int k = 0; k < ND; ++k) phe[l][q][k] = td.phe[l][q][k];
+  // the means go to the float form's limiter copy (float) and to mean64
+  element_body<P, double, false, float>(md, sd, ph, write_rhs, e, phe);
+}
+// List entry i -> block i mod gridDim.x, lane i / gridDim.x: consecutive entries (neighbouring
+// front elements) go to different SMs, and an SM's few front elements share one warp, so the
+// double work of a short list spreads over the whole GPU instead of a few SMs' FP64 pipes.
+__device__ __forceinline__ unsigned front_entry0() { return blockIdx.x + gridDim.x * threadIdx.x; }
+__device__ __forceinline__ unsigned front_stride() { return gridDim.x * blockDim.x; }
+
+// The listed front elements of one model (flat index = element), one per thread.
+template <int P>
+__global__ void __launch_bounds__(32) k_front(const DevMesh m, const StageArgs s, const Phys ph, const int write_rhs) {
+  const unsigned n = *s.fcnt;
+  for (unsigned i = front_entry0(); i < n; i += front_stride()) front_update_body<P>(m, s, ph, write_rhs, s.flist[i]);
+}
+
+// The float form's bounds keep the register counts these kernels had before the out-of-line front
+// path (whose needs would otherwise raise the whole kernel's allocation): 2 or 3 resident
+// 256-thread blocks per SM.
 template <int P, typename T, bool SPLIT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((P == 1 && SPLIT) ? 3 : 2) : 1)
     k_element(const DevMesh m, const StageArgs s, const Phys ph, const int write_rhs) {
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   load_phe<P, T>(s_phe);
   __syncthreads();
+  front_reset_prev(s);
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m.ne) return;
+  if (e >= m.nact) return;  // own elements and the first ghost layer of a part
   element_body<P, T, SPLIT>(m, s, ph, write_rhs, e, s_phe);
 }
 
@@ -887,14 +988,15 @@ __global__ void __launch_bounds__(256)
 // tile once (an edge between two tiles is computed identically by both) and leave the weighted
 // flux of each (element, local edge, Gauss point) in shared memory; after one barrier each thread
 // finishes its element (area integrals, gather in the fixed local-edge order, inverse mass, RK).
-// Shared memory: double state [3*ND][tile], float/double flux slots [3][NQE][3][tile], flags.
+// Shared memory: state [3*ND][tile] and flux slots [3][NQE][3][tile] in T, wet/dry flags [tile],
+// front codes [3][tile] (per local edge: the neighbour's flag or NBC_*).
 // ef: the float form with the inline vortex adds TILE_EF rows of the element phase's inputs (J^-1,
 // det J, vertex h_b, vertex x and y), copied asynchronously at the start of the tile.
 constexpr int TILE_EF = 14;
 template <int P, typename T>
 __host__ __device__ constexpr size_t tile_smem_bytes(int tile, bool ef = false) {
   return sizeof(T) * 3 * nd_of(P) * tile + sizeof(T) * 9 * nqe_of(P) * tile +
-         (ef && sizeof(T) == sizeof(float) ? sizeof(float) * TILE_EF * tile : 0) + tile;
+         (ef && sizeof(T) == sizeof(float) ? sizeof(float) * TILE_EF * tile : 0) + 4 * tile;
 }
 
 // Asynchronous 4-byte global -> shared copy (cp.async, cached in L1) and its completion.
@@ -925,7 +1027,8 @@ __device__ __forceinline__ void tile_modes(const T *s_u, int B, const double *u,
 template <int P, typename T>
 __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, const StageArgs &s, const Phys &ph,
                                           const int x, const int e0, const T *s_ud, T *s_slot,
-                                          const uint8_t *s_wd, const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
+                                          const uint8_t *s_wd, uint8_t *s_fr,
+                                          const T (*s_phe)[nqe_of(P)][nd_of(P)]) {
   constexpr int ND = nd_of(P), NQE = nqe_of(P);
   const Tab<T> &tb = ctab<T>(P);
   const int B = tl.tile, ne = m.ne;
@@ -956,6 +1059,10 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
     const uint8_t fa = s.wd ? (ina ? s_wd[a - e0] : s.wd[a]) : 0;
     const uint8_t fb = s.wd ? (inb ? s_wd[b - e0] : s.wd[b]) : 0;
     const bool flows = edge_flows<P>(ph, fa, fb, s.uin, ne, a, la, b, lb, hAd, hBd);
+    if (s.cls) {  // front test: each in-tile side records the other side's flag
+      if (ina) s_fr[la * B + a - e0] = fb;
+      if (inb) s_fr[lb * B + b - e0] = fa;
+    }
     T wb[3][ND];
     tile_modes<P, T>(s_ud, B, s.uin, ne, b, inb, b - e0, wb);
 #pragma unroll
@@ -988,6 +1095,7 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
       }
     }
   } else if (b == NBR_LAND || b == NBR_RIVER) {
+    if (s.cls) s_fr[la * B + a - e0] = b == NBR_LAND ? NBC_LAND : NBC_OPEN;
 #pragma unroll
     for (int q = 0; q < NQE; ++q) {
       T f[3];
@@ -999,6 +1107,7 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
       for (int v = 0; v < 3; ++v) slot(a - e0, la, q, v) = hl * tb.we[q] * f[v];
     }
   } else {
+    if (s.cls) s_fr[la * B + a - e0] = NBC_OPEN;
     const double ts = stage_time(s.clk, s.tau, s.tide_t);
     const T zt = from_d<T>(ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase));
 #pragma unroll
@@ -1026,8 +1135,9 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
   T *s_slot = s_ud + (size_t)3 * ND * B;
   float *s_ef = reinterpret_cast<float *>(s_slot + (size_t)9 * NQE * B);
   uint8_t *s_wd = reinterpret_cast<uint8_t *>(s_ef + (ef ? (size_t)TILE_EF * B : 0));
+  uint8_t *s_fr = s_wd + B;
   const int e0 = tile * B, i = threadIdx.x;
-  const int nloc = min(B, ne - e0);
+  const int nloc = min(B, m.nact - e0);  // the tiles cover the updated elements [0, nact)
   __shared__ double s_ctr[2];  // storm centre at the stage time, once per block (inline vortex)
   if (s.frc_inline && i == 0) storm_center(ph, stage_time(s.clk, s.tau, s.tide_t), s_ctr[0], s_ctr[1]);
   if (ef) {
@@ -1045,13 +1155,22 @@ __device__ __forceinline__ void tile_body(const DevMesh &m, const DevTiles &tl, 
 #pragma unroll
     for (int r = 0; r < 3 * ND; ++r) s_ud[r * B + i] = from_d<T>(__ldg(&s.uin[(size_t)r * ne + e0 + i]));
     s_wd[i] = s.wd ? s.wd[e0 + i] : 0;
+    s_fr[i] = s_fr[B + i] = s_fr[2 * B + i] = NBC_LAND;  // every slot is rewritten by its edge
   }
   __syncthreads();
   const int beg = tl.start[tile], end = tl.start[tile + 1];
-  for (int x = beg + i; x < end; x += B) tile_edge<P, T>(m, tl, s, ph, x, e0, s_ud, s_slot, s_wd, s_phe);
+  for (int x = beg + i; x < end; x += B) tile_edge<P, T>(m, tl, s, ph, x, e0, s_ud, s_slot, s_wd, s_fr, s_phe);
   if (ef) cp_async_wait_all();  // each thread reads only the rows it copied
   __syncthreads();
-  if (i < nloc) {
+  bool front = false;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (s.cls && i < nloc) {  // the front elements are left to the front kernels
+      front = is_front(s_wd[i], s_fr[i], s_fr[B + i], s_fr[2 * B + i], ph.rain != 0.0);
+      s.cls[e0 + i] = front ? 1 : 0;
+      if (front) front_append(s, s.fbase + e0 + i);
+    }
+  }
+  if (i < nloc && !front) {
     const int e = e0 + i;
     ElemCtx<P, T> c;
     if (ef) {
@@ -1098,6 +1217,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (P == 1 ? (WIDE ? 5 : 4)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T s_phe[3][nqe_of(P)][nd_of(P)];
   load_phe<P, T>(s_phe);
+  front_reset_prev(s);
   tile_body<P, T>(m, tl, s, ph, write_rhs, blockIdx.x, smem_raw, s_phe);
 }
 
@@ -1190,12 +1310,20 @@ __device__ __noinline__ void limiter_rebuild(const T d0, const T d1, const T d2,
   *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) * tb.lim_idet);
 }
 
+// fcls (float form, set when front elements exist): in the float path, skip the front elements
+// (cls 1: the front kernels limit them); in the double path of a front element, read a neighbour's
+// mean from `mean` (mean64) if it is at the front too, else from its updated state u (which the
+// float limiter, running after the front kernels, has not yet changed).
 template <int P, typename T>
 __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const T *mean, uint8_t *wd,
-                                           const Phys &ph, int *err, int do_lim, int do_wd, const int e) {
+                                           const Phys &ph, int *err, int do_lim, int do_wd, const int e,
+                                           const uint8_t *fcls = nullptr) {
   constexpr int ND = nd_of(P);
   const int ne = m.ne;
   const Tab<T> &tb = ctab<T>(P);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (fcls && fcls[e]) return;
+  }
   if (do_lim) {
     const T nu = T(1.5);
     int nb[3];
@@ -1211,7 +1339,15 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const T 
       const double d2 = u[(size_t)(v * ND + 2) * ne + e];
       T db3[3];  // neighbour means (stored in T: the float form rounds them once, when written)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) db3[j] = nb[j] >= 0 ? mean[(size_t)v * ne + nb[j]] : from_d<T>(d0);
+      for (int j = 0; j < 3; ++j) {
+        if (nb[j] < 0) {
+          db3[j] = from_d<T>(d0);
+        } else if (sizeof(T) == sizeof(double) && fcls && !fcls[nb[j]]) {
+          db3[j] = (T)u[(size_t)(v * ND) * ne + nb[j]];
+        } else {
+          db3[j] = mean[(size_t)v * ne + nb[j]];
+        }
+      }
       if constexpr (sizeof(T) == sizeof(double)) {
         // Filtered predicate (after Shewchuk's floating-point filters): a float evaluation with an
         // error margin well above its rounding proves, when it can, that minmod returns the midpoint
@@ -1364,13 +1500,37 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const T 
   }
 }
 
+// Double limiter and wet/dry of a front element (float form): the double limiter weights, the
+// front neighbours' means from mean64 and the others' from their updated states.
+template <int P>
+__device__ __forceinline__ void front_limwd_body(const DevMesh &m, double *u, const double *mean64,
+                                                 const uint8_t *cls, uint8_t *wd, const Phys &ph, int *err,
+                                                 int do_lim, int do_wd, int e) {
+  DevMesh md = m;
+  md.lima = m.lima_d;
+  limwd_body<P, double>(md, u, mean64, wd, ph, err, do_lim, do_wd, e, cls);
+}
+// The listed front elements of one model, one per thread (entries spread as in k_front).
+template <int P>
+__global__ void __launch_bounds__(32) k_limwd_front(const DevMesh m, double *u, const double *mean64,
+                                                    const uint8_t *cls, uint8_t *wd, const Phys ph, int *err,
+                                                    int do_lim, int do_wd, const int *flist,
+                                                    const unsigned *fcnt) {
+  const unsigned n = *fcnt;
+  for (unsigned i = front_entry0(); i < n; i += front_stride()) {
+    const int e = flist[i];
+    if (e < m.nown) front_limwd_body<P>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, e);
+  }
+}
+
+// float form: held to 64 registers (4 resident 256-thread blocks per SM), as without the front path
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_limwd(const DevMesh m, double *u, const T *mean,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_limwd(const DevMesh m, double *u, const T *mean,
                                                uint8_t *wd, const Phys ph, int *err, int do_lim,
-                                               int do_wd) {
+                                               int do_wd, const uint8_t *cls) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m.ne) return;
-  limwd_body<P, T>(m, u, mean, wd, ph, err, do_lim, do_wd, e);
+  if (e >= m.nown) return;  // a part limits only its own elements
+  limwd_body<P, T>(m, u, mean, wd, ph, err, do_lim, do_wd, e, cls);
 }
 
 // ------------------------------------------------------------------------ ensemble
@@ -1437,6 +1597,14 @@ __device__ __forceinline__ StageArgs member_stage(const MemberDev &md, const Ens
   sa.wd = md.ph.wetdry ? md.wd : nullptr;
   sa.eflux = nullptr;
   sa.emode = nullptr;
+  // front list (float form with wetting/drying): flat indices tile * block + i over all members;
+  // the previous stage's counter is reset in the element phase by block 0 (ens_phase)
+  sa.cls = md.cls;
+  sa.mean64 = md.mean64;
+  sa.flist = a.flist;
+  sa.fcnt = a.fcnt + stage;
+  sa.fcnt_prev = nullptr;
+  sa.fbase = md.etile0 * (int)blockDim.x;
   const bool inl = md.ph.hurricane && sizeof(T) == sizeof(float);
   sa.frc = (md.ph.hurricane && !inl) ? md.frc : nullptr;
   sa.frc_inline = inl ? 1 : 0;
@@ -1461,16 +1629,43 @@ __device__ __forceinline__ void load_member(MemberDev *dst, const MemberDev *src
   __syncthreads();
 }
 
+// Ensemble phases 3 and 4 (float form with wetting/drying): the double update, then the double
+// limiter and wet/dry, of the listed front elements of every member, one per thread.  Out of line,
+// so that the float phases keep their registers.
+template <int P, typename T>
+__device__ __noinline__ void ens_front_phase(const EnsArgs &a, int phase, int stage, int t_begin, int t_step) {
+  const unsigned n = *(volatile unsigned *)&a.fcnt[stage];
+  const int B = blockDim.x;
+  // entry i -> block i mod t_step, thread i / t_step (spread over the SMs, as in k_front)
+  for (unsigned i = t_begin + (unsigned)t_step * threadIdx.x; i < n; i += (unsigned)t_step * B) {
+    const int id = a.flist[i];
+    const MemberDev &md = a.mem[a.etile[id / B]];
+    const int e = id - md.etile0 * B;
+    if (phase == 3) {
+      front_update_body<P>(md.m, member_stage<T>(md, a, stage), md.ph, 0, e);
+    } else {
+      double *in, *out;
+      stage_buffers(stage, a.nstages, md.U0, md.U1, md.U2, in, out);
+      front_limwd_body<P>(md.m, out, md.mean64, md.cls, md.wd, md.ph, a.err, md.ph.limiter, md.ph.wetdry, e);
+    }
+  }
+}
+
 template <int P, typename T>
 __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage, int t_begin, int t_step,
                                           MemberDev *sd, const T (*s_phe)[nqe_of(P)][nd_of(P)],
                                           unsigned char *smem_raw) {
   if (phase == 1) {  // element update, one shared-memory tile per work item
+    if (a.any_front && blockIdx.x == 0 && threadIdx.x == 0) a.fcnt[(stage + a.nstages - 1) % a.nstages] = 0u;
     for (int t = t_begin; t < a.n_etile; t += t_step) {
       load_member(sd, &a.mem[a.etile[t]]);
       const StageArgs sa = member_stage<T>(*sd, a, stage);
       tile_body<P, T>(sd->m, sd->tl, sa, sd->ph, 0, t - sd->etile0, smem_raw, s_phe);
     }
+    return;
+  }
+  if (phase == 3 || phase == 4) {  // the listed front elements (float form): out of line
+    ens_front_phase<P, T>(a, phase, stage, t_begin, t_step);
     return;
   }
   if (phase == 0) {  // WIND at the nodes of members with a hurricane
@@ -1492,7 +1687,7 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
         double *in, *out;
         stage_buffers(stage, a.nstages, sd->U0, sd->U1, sd->U2, in, out);
         limwd_body<P, T>(sd->m, out, static_cast<const T *>(sd->mean), sd->wd, sd->ph, a.err, sd->ph.limiter,
-                         sd->ph.wetdry, e);
+                         sd->ph.wetdry, e, sd->cls);
       }
     }
   }
@@ -1518,6 +1713,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 5 : 2) : 1)) 
     }
     ens_phase<P, T>(a, 1, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
     if (!grid_barrier(a, skip)) return;
+    if (a.any_front) {  // front elements: double update, then double limiter and wet/dry
+      ens_phase<P, T>(a, 3, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
+      if (!grid_barrier(a, skip)) return;
+      ens_phase<P, T>(a, 4, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
+      if (!grid_barrier(a, skip)) return;
+    }
     if (a.any_limwd) {
       ens_phase<P, T>(a, 2, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
       if (stage < a.nstages - 1 && !grid_barrier(a, skip)) return;
@@ -1561,6 +1762,13 @@ cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int bloc
     }
     if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, sm, s>>>(a, 1, stage);
     else k_ens_phase<2, T><<<a.n_etile, block, sm, s>>>(a, 1, stage);
+    if (a.any_front) {  // a fixed grid striding over the front list
+      const int fb = std::min(a.n_etile, 304);
+      for (int ph = 3; ph <= 4; ++ph) {
+        if (p == 1) k_ens_phase<1, T><<<fb, block, sm, s>>>(a, ph, stage);
+        else k_ens_phase<2, T><<<fb, block, sm, s>>>(a, ph, stage);
+      }
+    }
     if (a.any_limwd) {
       if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, sm, s>>>(a, 2, stage);
       else k_ens_phase<2, T><<<a.n_etile, block, sm, s>>>(a, 2, stage);
@@ -1612,7 +1820,7 @@ void launch_edge_t(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, 
 template <typename T>
 void launch_element_t(int p, bool split, bool write_rhs, const DevMesh &m, const StageArgs &s, const Phys &ph,
                       const LaunchCfg &c) {
-  const int nb = nblocks(m.ne, c.block), wr = write_rhs ? 1 : 0;
+  const int nb = nblocks(m.nact, c.block), wr = write_rhs ? 1 : 0;
   if (p == 1) {
     if (split)
       k_element<1, T, true><<<nb, c.block, 0, c.stream>>>(m, s, ph, wr);
@@ -1675,13 +1883,41 @@ void launch_copy_means_t(int p, int ne, const double *u, void *mean, cudaStream_
 
 template <typename T>
 void launch_limwd_t(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const void *mean_v, uint8_t *wd,
-                    const Phys &ph, int *err, const LaunchCfg &c) {
+                    const Phys &ph, int *err, const LaunchCfg &c, const uint8_t *cls) {
   const T *mean = static_cast<const T *>(mean_v);
-  const int nb = nblocks(m.ne, c.block);
+  const int nb = nblocks(m.nown, c.block);
   if (p == 1)
-    k_limwd<1, T><<<nb, c.block, 0, c.stream>>>(m, u, mean, wd, ph, err, do_lim, do_wd);
+    k_limwd<1, T><<<nb, c.block, 0, c.stream>>>(m, u, mean, wd, ph, err, do_lim, do_wd, cls);
   else
-    k_limwd<2, T><<<nb, c.block, 0, c.stream>>>(m, u, mean, wd, ph, err, do_lim, do_wd);
+    k_limwd<2, T><<<nb, c.block, 0, c.stream>>>(m, u, mean, wd, ph, err, do_lim, do_wd, cls);
+}
+
+// The front kernels: a fixed grid (captured in the step graph; the list length is read on the
+// device) of one 32-thread block per SM, striding over the list.
+inline int front_blocks() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    n = sms > 0 ? sms : 152;
+  }
+  return n;
+}
+inline void launch_front_t(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, int write_rhs,
+                           cudaStream_t st) {
+  if (p == 1)
+    k_front<1><<<front_blocks(), 32, 0, st>>>(m, s, ph, write_rhs);
+  else
+    k_front<2><<<front_blocks(), 32, 0, st>>>(m, s, ph, write_rhs);
+}
+inline void launch_limwd_front_t(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean64,
+                                 const uint8_t *cls, uint8_t *wd, const Phys &ph, int *err, const int *flist,
+                                 const unsigned *fcnt, cudaStream_t st) {
+  if (p == 1)
+    k_limwd_front<1><<<front_blocks(), 32, 0, st>>>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, flist, fcnt);
+  else
+    k_limwd_front<2><<<front_blocks(), 32, 0, st>>>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, flist, fcnt);
 }
 
 }  // namespace dg

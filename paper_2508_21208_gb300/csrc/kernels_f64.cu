@@ -17,8 +17,8 @@ void launch_element_f64(int p, bool split, bool write_rhs, const DevMesh &m, con
   launch_element_t<double>(p, split, write_rhs, m, s, ph, c);
 }
 void launch_limwd_f64(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const void *mean,
-                      uint8_t *wd, const Phys &ph, int *err, const LaunchCfg &c) {
-  launch_limwd_t<double>(p, do_lim, do_wd, m, u, mean, wd, ph, err, c);
+                      uint8_t *wd, const Phys &ph, int *err, const LaunchCfg &c, const uint8_t *cls) {
+  launch_limwd_t<double>(p, do_lim, do_wd, m, u, mean, wd, ph, err, c, cls);
 }
 
 cudaError_t launch_ensemble_f64(int p, bool persistent, const EnsArgs &a, int block, int grid, cudaStream_t s) {

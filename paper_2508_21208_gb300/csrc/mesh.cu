@@ -39,7 +39,7 @@ uint64_t hilbert_index(uint32_t x, uint32_t y) {
 }  // namespace
 
 int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, HostMesh &H,
-                    std::string &msg) {
+                    std::string &msg, const int32_t *elem_class) {
   const int nn = m.n_nodes, ne = m.n_elems;
   if (nn < 3 || ne < 1 || !m.xy || !m.tri || !bathy || m.n_bedges < 0 ||
       (m.n_bedges > 0 && (!m.bedge || !m.bedge_type))) {
@@ -59,6 +59,23 @@ int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, Hos
   // ---- element order
   H.ne = ne;
   H.nn = nn;
+  H.nown = H.nact = ne;
+  if (elem_class) {
+    int cnt[3] = {0, 0, 0};
+    for (int e = 0; e < ne; ++e) {
+      if (elem_class[e] < 0 || elem_class[e] > 2) {
+        msg = "mesh: element class must be 0 (own), 1 or 2 (ghost layers)";
+        return DGSWEM_EINVAL;
+      }
+      cnt[elem_class[e]]++;
+    }
+    if (cnt[0] < 1) {
+      msg = "mesh: a part needs at least one own element";
+      return DGSWEM_EINVAL;
+    }
+    H.nown = cnt[0];
+    H.nact = cnt[0] + cnt[1];
+  }
   H.perm.resize(ne);
   std::iota(H.perm.begin(), H.perm.end(), 0);
   if (hilbert) {
@@ -77,6 +94,8 @@ int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, Hos
     }
     std::stable_sort(H.perm.begin(), H.perm.end(), [&](int a, int b) { return key[a] < key[b]; });
   }
+  if (elem_class)  // own, then ghost layer 1, then 2 (stable: Hilbert order within each class)
+    std::stable_sort(H.perm.begin(), H.perm.end(), [&](int a, int b) { return elem_class[a] < elem_class[b]; });
   H.iperm.assign(ne, 0);
   for (int i = 0; i < ne; ++i) H.iperm[H.perm[i]] = i;
   // ---- vertices and geometry (internal order)
@@ -292,18 +311,18 @@ int preprocess_mesh(const dgswem_mesh &m, const double *bathy, bool hilbert, Hos
 }
 
 void build_tile_edges(const HostMesh &H, int tile, TileEdges &T) {
-  const int ne = H.ne, nint = H.nint;
+  const int ne = H.ne, nint = H.nint, nact = H.nact;
   T.tile = tile;
-  T.ntiles = (ne + tile - 1) / tile;
+  T.ntiles = (nact + tile - 1) / tile;  // tiles cover the updated elements [0, nact)
   std::vector<int> count(T.ntiles + 1, 0);
-  auto tile_of = [&](int e) { return e / tile; };
+  auto tile_of = [&](int e) { return e < nact ? e / tile : -1; };  // -1: not updated here
   for (int d = 0; d < nint; ++d) {
-    const int a = H.edel[d], b = H.edel[nint + d];
-    count[tile_of(a)]++;
-    if (tile_of(b) != tile_of(a)) count[tile_of(b)]++;
+    const int ta = tile_of(H.edel[d]), tb = tile_of(H.edel[nint + d]);
+    if (ta >= 0) count[ta]++;
+    if (tb >= 0 && tb != ta) count[tb]++;
   }
   for (int l = 0; l < 3; ++l)
-    for (int e = 0; e < ne; ++e)
+    for (int e = 0; e < nact; ++e)
       if (H.nbr[(size_t)l * ne + e] < 0) count[tile_of(e)]++;
   T.start.assign(T.ntiles + 1, 0);
   for (int t = 0; t < T.ntiles; ++t) T.start[t + 1] = T.start[t] + count[t];
@@ -332,15 +351,15 @@ void build_tile_edges(const HostMesh &H, int tile, TileEdges &T) {
     const double nx = H.edgeo[d], ny = H.edgeo[nint + d], hl = H.edgeo[2 * (size_t)nint + d];
     const double ha = H.edhb[d], hbb = H.edhb[nint + d];
     const int ta = tile_of(a), tb = tile_of(b);
-    if (ta == tb) {
+    if (ta >= 0 && ta == tb) {
       put(ta, a, b, la, lb, true, true, nx, ny, hl, ha, hbb);
     } else {
-      put(ta, a, b, la, lb, true, false, nx, ny, hl, ha, hbb);
-      put(tb, a, b, la, lb, false, true, nx, ny, hl, ha, hbb);
+      if (ta >= 0) put(ta, a, b, la, lb, true, false, nx, ny, hl, ha, hbb);
+      if (tb >= 0) put(tb, a, b, la, lb, false, true, nx, ny, hl, ha, hbb);
     }
   }
   const double *g = H.geo.data();
-  for (int e = 0; e < ne; ++e)
+  for (int e = 0; e < nact; ++e)
     for (int l = 0; l < 3; ++l) {
       const int code = H.nbr[(size_t)l * ne + e];
       if (code >= 0) continue;

@@ -54,6 +54,20 @@ class Tuning(C.Structure):
                 ("autotune", C.c_int32)]
 
 
+class PartCounts(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("n_nodes", "n_elems", "n_bedges", "n_own", "n_ghost1", "n_ghost2",
+                                          "n_peers", "n_send", "n_recv")]
+
+
+class PartOut(C.Structure):
+    _fields_ = [("xy", C.POINTER(C.c_double)), ("tri", C.POINTER(C.c_int32)), ("bedge", C.POINTER(C.c_int32)),
+                ("bedge_type", C.POINTER(C.c_int32)), ("bathy", C.POINTER(C.c_double)),
+                ("elem_global", C.POINTER(C.c_int32)), ("elem_class", C.POINTER(C.c_int32)),
+                ("node_global", C.POINTER(C.c_int32)), ("peer", C.POINTER(C.c_int32)),
+                ("send_count", C.POINTER(C.c_int32)), ("recv_count", C.POINTER(C.c_int32)),
+                ("send_elems", C.POINTER(C.c_int32)), ("recv_elems", C.POINTER(C.c_int32))]
+
+
 class Init(C.Structure):
     _fields_ = [("modal", C.POINTER(C.c_double)), ("nodal", C.POINTER(C.c_double)), ("t0", C.c_double)]
 
@@ -91,9 +105,15 @@ SIGNATURES = [
                                          C.POINTER(Params), C.POINTER(Init), C.POINTER(Tuning), C.POINTER(_vp)]),
     ("dgswem_ensemble_step", C.c_int, [_vp, C.c_int32]),
     ("dgswem_ensemble_get_state", C.c_int, [_vp, C.c_int32, _dp, _dp, _dp]),
+    ("dgswem_ensemble_get_flags", C.c_int, [_vp, C.c_int32, C.POINTER(C.c_uint8)]),
     ("dgswem_ensemble_info", C.c_int, [_vp, C.c_int32, _dp, _dp, C.POINTER(C.c_int64)]),
     ("dgswem_ensemble_set_fault", C.c_int, [_vp, C.c_int32]),
     ("dgswem_mass_noalloc", C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, _vp]),
+    ("dgswem_partition_rcb", C.c_int, [C.POINTER(Mesh), C.c_int32, C.POINTER(C.c_int32)]),
+    ("dgswem_part_sizes", C.c_int, [C.POINTER(Mesh), C.POINTER(C.c_int32), C.c_int32, C.c_int32,
+                                    C.POINTER(PartCounts)]),
+    ("dgswem_part_build", C.c_int, [C.POINTER(Mesh), _dp, C.POINTER(C.c_int32), C.c_int32, C.c_int32,
+                                    C.POINTER(PartOut)]),
 ]
 
 
@@ -323,6 +343,12 @@ class Ensemble(_Handle):
         ne = self.meshes[self.members[i][0]].n_elems
         out = np.empty((3, self.nd, ne))
         self._check(self.lib.dgswem_ensemble_get_state(self.h, int(i), _ptr(out[0]), _ptr(out[1]), _ptr(out[2])))
+        return out
+
+    def flags(self, i: int) -> np.ndarray:
+        ne = self.meshes[self.members[i][0]].n_elems
+        out = np.empty(ne, np.uint8)
+        self._check(self.lib.dgswem_ensemble_get_flags(self.h, int(i), _ptr(out, C.c_uint8)))
         return out
 
     def info(self, i: int):
