@@ -373,6 +373,43 @@ typedef struct {
 DGSWEM_API int dgswem_part_build(const dgswem_mesh *mesh, const double *bathy, const int32_t *part,
                                  int32_t n_parts, int32_t rank, const dgswem_part_out *out);
 
+/* One part of a partitioned domain: dgswem_create with the sub-mesh of dgswem_part_build (its
+ * elements in the sub-mesh order), their classes, and the send / receive lists as sub-mesh element
+ * indices in the order of the packed buffers (send: own elements; receive: ghost elements).  The
+ * part needs a fixed time step (params->dt > 0: the global one, the same on every part).  The
+ * context then updates its own elements and the first ghost layer and limits and wets/dries its own
+ * elements; dgswem_mass sums its own elements (the caller adds the parts' sums); the state calls
+ * see every sub-mesh element.  A part steps stage by stage (dgswem_stage_compute / _finish), not
+ * with dgswem_step (DGSWEM_ESTATE).  Errors: as dgswem_create; DGSWEM_EINVAL also for a missing
+ * class array, dt <= 0, or a list entry out of range or of the wrong class. */
+typedef struct {
+  const int32_t *elem_class;  /* [n_elems]: 0 own, 1 first ghost layer, 2 second */
+  int32_t n_send;
+  const int32_t *send_elems;  /* [n_send] own elements, in send-buffer order */
+  int32_t n_recv;
+  const int32_t *recv_elems;  /* [n_recv] ghost elements, in receive-buffer order */
+} dgswem_part;
+DGSWEM_API int dgswem_create_part(const dgswem_mesh *mesh, const double *bathy, const dgswem_params *params,
+                                  const dgswem_init *init, const dgswem_tuning *tuning, const dgswem_part *part,
+                                  dgswem_ctx **out);
+/* Bytes of the packed send and receive buffers: one record of 3 ndof + 1 doubles per listed element
+ * (its modal state, then its wet/dry flag as a double), as in the paper's packElems (Listing
+ * code:pack).  DGSWEM_EINVAL for a context that is not a part. */
+DGSWEM_API int dgswem_halo_sizes(dgswem_ctx *ctx, size_t *send_bytes, size_t *recv_bytes);
+/* Bind caller-owned device buffers of dgswem_halo_sizes bytes (8-byte aligned; the caller keeps
+ * them alive, and moves the bytes between parts itself: NCCL send/recv, MPI or copies). */
+DGSWEM_API int dgswem_halo_attach(dgswem_ctx *ctx, void *d_send, void *d_recv);
+/* One Runge-Kutta stage of a part, in two calls around the caller's exchange (Sec. 5.3, Listing
+ * code:mpi: pack, exchange, unpack).  dgswem_stage_compute issues the stage's kernels on the own
+ * elements and the first ghost layer (element update, limiter and wet/dry on the own elements) and
+ * packs the send list's records into the send buffer; the caller then delivers each peer's packed
+ * records into this part's receive buffer, ordered on the context stream; dgswem_stage_finish
+ * unpacks them into the ghost elements' states and flags.  After the scheme's last stage the step is
+ * complete.  Both calls are asynchronous.  Errors: DGSWEM_ESTATE (not attached, calls out of order,
+ * no halo buffers), DGSWEM_EINVAL (not a part). */
+DGSWEM_API int dgswem_stage_compute(dgswem_ctx *ctx);
+DGSWEM_API int dgswem_stage_finish(dgswem_ctx *ctx);
+
 /* ---- allocation-free mass sums ----
  * The paper has no counterpart: this is a service for callers that may not allocate device
  * memory.  Examples are a host model or coupler that owns the whole GPU memory budget and

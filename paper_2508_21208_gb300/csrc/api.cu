@@ -224,6 +224,8 @@ static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
   c->mean64 = c->mixed ? k.take<double>(3 * (size_t)ne) : nullptr;
   c->flist = k.take<int>(ne);
   c->fcnt = k.take<unsigned>(MAX_STAGES);
+  c->d_send_idx = k.take<int>(c->halo_send.size());
+  c->d_recv_idx = k.take<int>(c->halo_recv.size());
   c->wd = k.take<uint8_t>(ne);
   c->wd_stage = k.take<uint8_t>(ne);
   c->eflux = k.take<char>(tsz * 3 * NQE * nint);
@@ -309,20 +311,26 @@ static void mark(dgswem_ctx *c, const char *name, std::vector<const char *> *nam
   ++*ev_i;
 }
 
-// Issue the kernels of one time step (the scheme's stages) on the context stream.
-static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const char *> *names) {
+// State buffer that stage `stage` writes: intermediate stages alternate U1 / U2, the last one
+// writes u^(n+1) over U0 (each element reads only its own u^n there).
+static double *stage_out(dgswem_ctx *c, int stage) {
+  return stage == c->nst - 1 ? c->U0 : (stage % 2 == 0 ? c->U1 : c->U2);
+}
+
+// Issue the kernels of one stage on the context stream (ev_i: next kernel-timing event).
+static void enqueue_stage(dgswem_ctx *c, int variant, int block, int stage, std::vector<const char *> *names,
+                          int *ev_i) {
   const bool split = variant == DGSWEM_VARIANT_SPLIT;
   const LaunchCfg cfg{block, c->st};
   const Phys &ph = c->ph;
-  int ev_i = 0;
-  for (int stage = 0; stage < c->nst; ++stage) {
+  {
     // stage 0 reads u^n (U0); intermediate stages alternate U1 / U2; the last writes over U0
     double *uin = stage == 0 ? c->U0 : ((stage - 1) % 2 == 0 ? c->U1 : c->U2);
-    double *out = stage == c->nst - 1 ? c->U0 : (stage % 2 == 0 ? c->U1 : c->U2);
+    double *out = stage_out(c, stage);
     const Clock clk{c->step, c->t0, c->dt};
     const bool inline_frc = ph.hurricane && c->mixed;  // mixed form: vortex evaluated per element vertex
     if (ph.hurricane && !inline_frc) {
-      mark(c, kname_forcing, names, &ev_i);
+      mark(c, kname_forcing, names, ev_i);
       launch_forcing(c->mixed, c->dm, ph, clk, c->rtau[stage], 0.0, c->frc, cfg);
     }
     StageArgs sa{};
@@ -353,30 +361,36 @@ static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const
     sa.fcnt_prev = front ? c->fcnt + (stage + c->nst - 1) % c->nst : nullptr;
     sa.fbase = 0;
     if (variant == DGSWEM_VARIANT_TILED || variant == DGSWEM_VARIANT_TILED_WIDE) {
-      mark(c, kname_element, names, &ev_i);
+      mark(c, kname_element, names, ev_i);
       launch_tile(c->mixed, c->P, variant == DGSWEM_VARIANT_TILED_WIDE, false, c->dm, c->tiles, sa, ph, cfg);
     } else {
       if (split && c->dm.nint > 0) {
-        mark(c, kname_edge, names, &ev_i);
+        mark(c, kname_edge, names, ev_i);
         launch_edge(c->mixed, c->P, c->dm, sa, ph, cfg);
       }
-      mark(c, kname_element, names, &ev_i);
+      mark(c, kname_element, names, ev_i);
       launch_element(c->mixed, c->P, split, false, c->dm, sa, ph, cfg);
     }
     if (front) {
-      mark(c, kname_front, names, &ev_i);
+      mark(c, kname_front, names, ev_i);
       launch_front(c->P, c->dm, sa, ph, 0, c->st);
     }
     if (ph.limiter || ph.wetdry) {
       if (front) {  // before the float limiter, which changes the non-front states they read
-        mark(c, kname_limwd_front, names, &ev_i);
+        mark(c, kname_limwd_front, names, ev_i);
         launch_limwd_front(c->P, ph.limiter, ph.wetdry, c->dm, out, c->mean64, c->cls, c->wd, ph, c->err, c->flist,
                            sa.fcnt, c->st);
       }
-      mark(c, kname_limwd, names, &ev_i);
+      mark(c, kname_limwd, names, ev_i);
       launch_limwd(c->mixed, c->P, ph.limiter, ph.wetdry, c->dm, out, c->mean, c->wd, ph, c->err, cfg, sa.cls);
     }
   }
+}
+
+// Issue the kernels of one time step (the scheme's stages) on the context stream.
+static int enqueue_step(dgswem_ctx *c, int variant, int block, std::vector<const char *> *names) {
+  int ev_i = 0;
+  for (int stage = 0; stage < c->nst; ++stage) enqueue_stage(c, variant, block, stage, names, &ev_i);
   mark(c, kname_advance, names, &ev_i);
   launch_advance(c->step, c->st);
   if (names) {
@@ -522,15 +536,21 @@ int upload_mesh(dgswem_ctx *c, const HostMesh &H, const DevMesh &m, int *perm, i
 }
 
 // ------------------------------------------------------------------ C ABI
-extern "C" {
 
-int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_params *params,
-                  const dgswem_init *init, const dgswem_tuning *tuning, dgswem_ctx **out) {
+// dgswem_create, and dgswem_create_part when part is set.
+static int create_common(const dgswem_mesh *mesh, const double *bathy, const dgswem_params *params,
+                         const dgswem_init *init, const dgswem_tuning *tuning, const dgswem_part *part,
+                         dgswem_ctx **out) {
   if (!out) return DGSWEM_EINVAL;
   *out = nullptr;
   if (!mesh || !bathy) return DGSWEM_EINVAL;
   std::string msg;
   if (check_params(params, msg)) return DGSWEM_EINVAL;
+  if (part) {  // a part runs with the global time step, fixed by the caller
+    if (!(params->dt > 0) || !part->elem_class || part->n_send < 0 || part->n_recv < 0 ||
+        (part->n_send > 0 && !part->send_elems) || (part->n_recv > 0 && !part->recv_elems))
+      return DGSWEM_EINVAL;
+  }
   dgswem_ctx *c = new dgswem_ctx();
   c->prm = *params;
   if (tuning) c->tun = *tuning;
@@ -544,10 +564,24 @@ int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_par
   c->ND = nd_of(c->P);
   c->mixed = params->precision == DGSWEM_FP32_MIXED;
   c->nst = rk_stage_table(*params, c->ra, c->rb, c->rc, c->rtau);
-  int r = preprocess_mesh(*mesh, bathy, c->tun.reorder != 2, c->hm, msg);
+  int r = preprocess_mesh(*mesh, bathy, c->tun.reorder != 2, c->hm, msg, part ? part->elem_class : nullptr);
   if (r) {
     delete c;
     return r;
+  }
+  if (part) {
+    // send: own elements; receive: ghost elements (caller indices, checked against the classes)
+    c->part = true;
+    for (int i = 0; i < part->n_send; ++i) {
+      const int e = part->send_elems[i];
+      if (e < 0 || e >= c->hm.ne || part->elem_class[e] != 0) { delete c; return DGSWEM_EINVAL; }
+      c->halo_send.push_back(c->hm.iperm[e]);
+    }
+    for (int i = 0; i < part->n_recv; ++i) {
+      const int e = part->recv_elems[i];
+      if (e < 0 || e >= c->hm.ne || part->elem_class[e] == 0) { delete c; return DGSWEM_EINVAL; }
+      c->halo_recv.push_back(c->hm.iperm[e]);
+    }
   }
   c->ph = make_phys(*params);
   c->t0 = init ? init->t0 : 0.0;
@@ -571,6 +605,23 @@ int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_par
   layout(c, nullptr, &c->need);
   *out = c;
   return 0;
+}
+
+extern "C" {
+
+int dgswem_create(const dgswem_mesh *mesh, const double *bathy, const dgswem_params *params,
+                  const dgswem_init *init, const dgswem_tuning *tuning, dgswem_ctx **out) {
+  return create_common(mesh, bathy, params, init, tuning, nullptr, out);
+}
+
+int dgswem_create_part(const dgswem_mesh *mesh, const double *bathy, const dgswem_params *params,
+                       const dgswem_init *init, const dgswem_tuning *tuning, const dgswem_part *part,
+                       dgswem_ctx **out) {
+  if (!part) {
+    if (out) *out = nullptr;
+    return DGSWEM_EINVAL;
+  }
+  return create_common(mesh, bathy, params, init, tuning, part, out);
 }
 
 int dgswem_workspace_size(const dgswem_ctx *ctx, size_t *bytes) {
@@ -668,6 +719,12 @@ int dgswem_attach(dgswem_ctx *c, void *d_workspace, size_t bytes, void *stream) 
   layout(c, c->ws, &sz);
   cudaStream_t s = c->st;
   if (int r = upload_static(c)) return r;
+  if (c->part) {
+    if (!c->halo_send.empty())
+      cudaMemcpyAsync(c->d_send_idx, c->halo_send.data(), c->halo_send.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (!c->halo_recv.empty())
+      cudaMemcpyAsync(c->d_recv_idx, c->halo_recv.data(), c->halo_recv.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  }
   c->tiles.tile = 0;
   const size_t nu = 3 * (size_t)c->ND * c->hm.ne;
   cudaMemsetAsync(c->step, 0, sizeof(long long), s);
@@ -712,6 +769,7 @@ int dgswem_step(dgswem_ctx *c, int32_t n) {
   if (c->sticky) return c->sticky;
   if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "step before attach");
   if (n < 0) return DGSWEM_EINVAL;
+  if (c->part) return ctx_fail(c, DGSWEM_ESTATE, "a part steps with dgswem_stage_compute / dgswem_stage_finish");
   for (int i = 0; i < n; ++i) {
     cudaError_t e = cudaGraphLaunch(c->exec, c->st);
     if (e != cudaSuccess) return ctx_cuda(c, e, "graph launch");
@@ -961,6 +1019,58 @@ int dgswem_tune_log(dgswem_ctx *c, int32_t *variant, int32_t *block, float *ms, 
     if (ms) ms[i] = log[i].ms_per_step;
   }
   return 0;
+}
+
+// ---- a part of a partitioned domain
+int dgswem_halo_sizes(dgswem_ctx *c, size_t *send_bytes, size_t *recv_bytes) {
+  if (!c || !send_bytes || !recv_bytes) return DGSWEM_EINVAL;
+  if (!c->part) return ctx_fail(c, DGSWEM_EINVAL, "not a part (dgswem_create_part)");
+  const size_t rec = (3 * (size_t)c->ND + 1) * sizeof(double);
+  *send_bytes = c->halo_send.size() * rec;
+  *recv_bytes = c->halo_recv.size() * rec;
+  return 0;
+}
+
+int dgswem_halo_attach(dgswem_ctx *c, void *d_send, void *d_recv) {
+  if (!c) return DGSWEM_EINVAL;
+  if (!c->part) return ctx_fail(c, DGSWEM_EINVAL, "not a part (dgswem_create_part)");
+  if ((!c->halo_send.empty() && !d_send) || (!c->halo_recv.empty() && !d_recv) ||
+      reinterpret_cast<uintptr_t>(d_send) % 8 || reinterpret_cast<uintptr_t>(d_recv) % 8)
+    return ctx_fail(c, DGSWEM_EINVAL, "halo buffers: null or not 8-byte aligned");
+  c->d_send_buf = static_cast<double *>(d_send);
+  c->d_recv_buf = static_cast<double *>(d_recv);
+  return 0;
+}
+
+int dgswem_stage_compute(dgswem_ctx *c) {
+  if (!c) return DGSWEM_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->attached) return ctx_fail(c, DGSWEM_ESTATE, "not attached");
+  if (!c->part) return ctx_fail(c, DGSWEM_EINVAL, "not a part (dgswem_create_part)");
+  if (c->stage_open) return ctx_fail(c, DGSWEM_ESTATE, "dgswem_stage_finish first");
+  if ((!c->halo_send.empty() && !c->d_send_buf) || (!c->halo_recv.empty() && !c->d_recv_buf))
+    return ctx_fail(c, DGSWEM_ESTATE, "dgswem_halo_attach first");
+  int ev_i = 0;
+  enqueue_stage(c, c->variant, c->block, c->stage_i, nullptr, &ev_i);
+  launch_halo_pack(c->ND, c->hm.ne, stage_out(c, c->stage_i), c->wd, c->d_send_idx, (int)c->halo_send.size(),
+                   c->d_send_buf, c->st);
+  c->stage_open = true;
+  return ctx_cuda(c, cudaGetLastError(), "stage compute");
+}
+
+int dgswem_stage_finish(dgswem_ctx *c) {
+  if (!c) return DGSWEM_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->stage_open) return ctx_fail(c, DGSWEM_ESTATE, "dgswem_stage_compute first");
+  launch_halo_unpack(c->ND, c->hm.ne, stage_out(c, c->stage_i), c->wd, c->d_recv_idx, (int)c->halo_recv.size(),
+                     c->d_recv_buf, c->st);
+  c->stage_open = false;
+  if (++c->stage_i == c->nst) {
+    c->stage_i = 0;
+    launch_advance(c->step, c->st);
+    c->steps_done++;
+  }
+  return ctx_cuda(c, cudaGetLastError(), "stage finish");
 }
 
 int dgswem_graph_info(dgswem_ctx *c, int32_t *kps, int32_t *variant, int32_t *block) {

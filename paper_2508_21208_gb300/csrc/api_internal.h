@@ -77,6 +77,14 @@ struct dgswem_ctx {
   std::vector<cudaEvent_t> ev;
   std::vector<const char *> knames;
   std::vector<TuneEntry> tune_log;
+  // a part of a partitioned domain (dgswem_create_part): halo lists in internal element order,
+  // their device copies, the caller's packed buffers and the stage in progress
+  bool part = false;
+  std::vector<int> halo_send, halo_recv;
+  int *d_send_idx = nullptr, *d_recv_idx = nullptr;
+  double *d_send_buf = nullptr, *d_recv_buf = nullptr;
+  int stage_i = 0;
+  bool stage_open = false;
   // errors
   int sticky = 0;
   std::string errmsg;

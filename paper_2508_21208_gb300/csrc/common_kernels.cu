@@ -146,6 +146,38 @@ void launch_permute_u8(const uint8_t *src, uint8_t *dst, const int *map, int ne,
   k_permute_u8<<<nblk(ne, 256), 256, 0, s>>>(src, dst, map, ne);
 }
 
+// Ghost exchange of a part (Sec. 5.3, the packElems / unpackElems of Listing code:pack): record k of
+// the contiguous buffer holds element idx[k]'s modal state, row by row ([3 nd] doubles), then its
+// wet/dry flag as a double.
+__global__ void k_halo_pack(int rows, int ne, const double *u, const uint8_t *wd, const int *idx, int n,
+                            double *buf) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int rec = rows + 1;
+  if (i >= (long)n * rec) return;
+  const int k = (int)(i / rec), r = (int)(i - (long)k * rec), e = idx[k];
+  buf[i] = r < rows ? u[(size_t)r * ne + e] : (double)wd[e];
+}
+
+__global__ void k_halo_unpack(int rows, int ne, double *u, uint8_t *wd, const int *idx, int n, const double *buf) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int rec = rows + 1;
+  if (i >= (long)n * rec) return;
+  const int k = (int)(i / rec), r = (int)(i - (long)k * rec), e = idx[k];
+  if (r < rows)
+    u[(size_t)r * ne + e] = buf[i];
+  else
+    wd[e] = (uint8_t)buf[i];
+}
+
+void launch_halo_pack(int nd, int ne, const double *u, const uint8_t *wd, const int *idx, int n, double *buf,
+                      cudaStream_t s) {
+  if (n > 0) k_halo_pack<<<nblk((long)n * (3 * nd + 1), 256), 256, 0, s>>>(3 * nd, ne, u, wd, idx, n, buf);
+}
+void launch_halo_unpack(int nd, int ne, double *u, uint8_t *wd, const int *idx, int n, const double *buf,
+                        cudaStream_t s) {
+  if (n > 0) k_halo_unpack<<<nblk((long)n * (3 * nd + 1), 256), 256, 0, s>>>(3 * nd, ne, u, wd, idx, n, buf);
+}
+
 __global__ void k_advance(long long *step) { *step += 1; }
 
 void launch_advance(long long *step, cudaStream_t s) { k_advance<<<1, 1, 0, s>>>(step); }

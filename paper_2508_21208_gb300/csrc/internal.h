@@ -337,6 +337,11 @@ void launch_permute(const double *src, double *dst, const int *map, int rows, in
                     cudaStream_t s);
 void launch_permute_u8(const uint8_t *src, uint8_t *dst, const int *map, int ne, cudaStream_t s);
 void launch_advance(long long *step, cudaStream_t s);
+// pack / unpack the halo records (state rows and wet/dry flag) of the elements idx[0..n)
+void launch_halo_pack(int nd, int ne, const double *u, const uint8_t *wd, const int *idx, int n, double *buf,
+                      cudaStream_t s);
+void launch_halo_unpack(int nd, int ne, double *u, uint8_t *wd, const int *idx, int n, const double *buf,
+                        cudaStream_t s);
 int mass_partial_count(int ne);
 
 }  // namespace dg

@@ -72,6 +72,11 @@ class Init(C.Structure):
     _fields_ = [("modal", C.POINTER(C.c_double)), ("nodal", C.POINTER(C.c_double)), ("t0", C.c_double)]
 
 
+class PartSpec(C.Structure):
+    _fields_ = [("elem_class", C.POINTER(C.c_int32)), ("n_send", C.c_int32), ("send_elems", C.POINTER(C.c_int32)),
+                ("n_recv", C.c_int32), ("recv_elems", C.POINTER(C.c_int32))]
+
+
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
 _lib = None
@@ -114,6 +119,12 @@ SIGNATURES = [
                                     C.POINTER(PartCounts)]),
     ("dgswem_part_build", C.c_int, [C.POINTER(Mesh), _dp, C.POINTER(C.c_int32), C.c_int32, C.c_int32,
                                     C.POINTER(PartOut)]),
+    ("dgswem_create_part", C.c_int, [C.POINTER(Mesh), _dp, C.POINTER(Params), C.POINTER(Init), C.POINTER(Tuning),
+                                     C.POINTER(PartSpec), C.POINTER(_vp)]),
+    ("dgswem_halo_sizes", C.c_int, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    ("dgswem_halo_attach", C.c_int, [_vp, _vp, _vp]),
+    ("dgswem_stage_compute", C.c_int, [_vp]),
+    ("dgswem_stage_finish", C.c_int, [_vp]),
 ]
 
 
@@ -358,3 +369,138 @@ class Ensemble(_Handle):
 
     def set_fault(self, on: bool):
         self._check(self.lib.dgswem_ensemble_set_fault(self.h, 1 if on else 0))
+
+
+# ---------------------------------------------------------------- domain decomposition (Sec. 5.3)
+class SubMesh:
+    """A part's sub-mesh (the fields _MeshArrays reads)."""
+
+    def __init__(self, xy, tri, bedge, bedge_type):
+        self.xy, self.tri, self.bedge, self.bedge_type = xy, tri, bedge, bedge_type
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def n_elems(self) -> int:
+        return int(self.tri.shape[0])
+
+
+class Part:
+    """dgswem_part_build's output for one part: sub-mesh, bathymetry, global ids, element classes
+    and, per peer, the send and receive lists (sub-mesh element indices)."""
+
+    def __init__(self, mesh, bathy, elem_global, elem_class, node_global, peers, send, recv):
+        self.mesh, self.bathy = mesh, bathy
+        self.elem_global, self.elem_class, self.node_global = elem_global, elem_class, node_global
+        self.peers = peers  # list of peer ranks
+        self.send = send    # list (per peer) of int32 arrays
+        self.recv = recv
+
+    @property
+    def send_elems(self):
+        return np.concatenate(self.send).astype(np.int32) if self.send else np.zeros(0, np.int32)
+
+    @property
+    def recv_elems(self):
+        return np.concatenate(self.recv).astype(np.int32) if self.recv else np.zeros(0, np.int32)
+
+
+def partition_rcb(mesh, n_parts: int) -> np.ndarray:
+    lib = load_library()
+    m = _MeshArrays(mesh)
+    part = np.empty(mesh.n_elems, np.int32)
+    rc = lib.dgswem_partition_rcb(C.byref(m.s), int(n_parts), _ptr(part, C.c_int32))
+    if rc != DGSWEM_OK:
+        raise DgswemError(rc, "dgswem_partition_rcb")
+    return part
+
+
+def build_part(mesh, bathy, part, n_parts: int, rank: int) -> Part:
+    lib = load_library()
+    m = _MeshArrays(mesh)
+    part = np.ascontiguousarray(part, np.int32)
+    hb = np.ascontiguousarray(bathy, np.float64)
+    cnt = PartCounts()
+    rc = lib.dgswem_part_sizes(C.byref(m.s), _ptr(part, C.c_int32), int(n_parts), int(rank), C.byref(cnt))
+    if rc != DGSWEM_OK:
+        raise DgswemError(rc, "dgswem_part_sizes")
+    xy = np.empty((cnt.n_nodes, 2))
+    tri = np.empty((cnt.n_elems, 3), np.int32)
+    be = np.empty((cnt.n_bedges, 2), np.int32)
+    bt = np.empty(cnt.n_bedges, np.int32)
+    sub_hb = np.empty(cnt.n_nodes)
+    eg = np.empty(cnt.n_elems, np.int32)
+    ec = np.empty(cnt.n_elems, np.int32)
+    ng = np.empty(cnt.n_nodes, np.int32)
+    peer = np.empty(max(cnt.n_peers, 1), np.int32)
+    sc = np.empty(max(cnt.n_peers, 1), np.int32)
+    rcnt = np.empty(max(cnt.n_peers, 1), np.int32)
+    se = np.empty(max(cnt.n_send, 1), np.int32)
+    re = np.empty(max(cnt.n_recv, 1), np.int32)
+    i32 = C.c_int32
+    out = PartOut(_ptr(xy), _ptr(tri, i32), _ptr(be, i32), _ptr(bt, i32), _ptr(sub_hb), _ptr(eg, i32), _ptr(ec, i32),
+                  _ptr(ng, i32), _ptr(peer, i32), _ptr(sc, i32), _ptr(rcnt, i32), _ptr(se, i32), _ptr(re, i32))
+    rc = lib.dgswem_part_build(C.byref(m.s), _ptr(hb), _ptr(part, C.c_int32), int(n_parts), int(rank), C.byref(out))
+    if rc != DGSWEM_OK:
+        raise DgswemError(rc, "dgswem_part_build")
+    peers = [int(x) for x in peer[:cnt.n_peers]]
+    send, recv, a, b = [], [], 0, 0
+    for k in range(cnt.n_peers):
+        send.append(se[a:a + sc[k]].copy())
+        recv.append(re[b:b + rcnt[k]].copy())
+        a += sc[k]
+        b += rcnt[k]
+    return Part(SubMesh(xy, tri, be, bt), sub_hb, eg, ec, ng, peers, send, recv)
+
+
+class PartModel(Model):
+    """One part of a partitioned model (dgswem_create_part + dgswem_attach + dgswem_halo_attach).
+
+    The packed send / receive buffers are torch tensors on the device (float64, one record of
+    3 ndof + 1 values per listed element).  A stage is stage_compute(), the delivery of the peers'
+    records into recv_buf, then stage_finish().  The delivery must be ordered on the context's
+    stream: pass an explicit torch stream (torch's default stream reaches the library as NULL,
+    for which the library creates a private non-blocking stream) and enqueue the copies or NCCL
+    calls on it."""
+
+    def __init__(self, part: Part, params: dict, init_nodal=None, init_modal=None, t0=0.0, variant=0, block=0,
+                 reorder=0, stream=None):
+        _Handle.__init__(self)
+        mesh = part.mesh
+        m = _MeshArrays(mesh)
+        hb = np.ascontiguousarray(part.bathy, np.float64)
+        self.prm = make_params(params)
+        nodal = None if init_nodal is None else np.ascontiguousarray(init_nodal, np.float64)
+        modal = None if init_modal is None else np.ascontiguousarray(init_modal, np.float64)
+        ini = Init(_ptr(modal), _ptr(nodal), float(t0))
+        tun = Tuning(int(variant), int(block), int(reorder), 0)
+        self._cls = np.ascontiguousarray(part.elem_class, np.int32)
+        self._se = part.send_elems
+        self._re = part.recv_elems
+        spec = PartSpec(_ptr(self._cls, C.c_int32), len(self._se), _ptr(self._se, C.c_int32), len(self._re),
+                        _ptr(self._re, C.c_int32))
+        rc = self.lib.dgswem_create_part(C.byref(m.s), _ptr(hb), C.byref(self.prm), C.byref(ini), C.byref(tun),
+                                         C.byref(spec), C.byref(self.h))
+        if rc != DGSWEM_OK:
+            raise DgswemError(rc, "dgswem_create_part")
+        self.ne = mesh.n_elems
+        self.nn = mesh.n_nodes
+        self.nd = (params["p"] + 1) * (params["p"] + 2) // 2
+        self.part = part
+        self._attach(stream)
+        torch = _torch_cuda()
+        sb, rb = C.c_size_t(), C.c_size_t()
+        self._check(self.lib.dgswem_halo_sizes(self.h, C.byref(sb), C.byref(rb)))
+        rec = 3 * self.nd + 1
+        self.send_buf = torch.zeros(max(sb.value // 8, 1), dtype=torch.float64, device="cuda")
+        self.recv_buf = torch.zeros(max(rb.value // 8, 1), dtype=torch.float64, device="cuda")
+        self.record = rec
+        self._check(self.lib.dgswem_halo_attach(self.h, _vp(self.send_buf.data_ptr()), _vp(self.recv_buf.data_ptr())))
+
+    def stage_compute(self):
+        self._check(self.lib.dgswem_stage_compute(self.h))
+
+    def stage_finish(self):
+        self._check(self.lib.dgswem_stage_finish(self.h))
