@@ -211,6 +211,50 @@ def run_form(case, steps, warmup, stream, flush, per_kernel=True, dist=None, **k
     return m, ms, kt, (kps, variant, block)
 
 
+def run_stats(ms, units_per_step, runs=5):
+    """The timed steps split into `runs` consecutive runs of equal length: each run's rate, their
+    median and spread (the value reported stays the whole timed region's)."""
+    k = len(ms) // runs
+    if k < 1:
+        return None
+    rates = [units_per_step * k / (sum(ms[i * k:(i + 1) * k]) * 1e-3) for i in range(runs)]
+    return {"runs": runs, "steps_per_run": k, "rates": rates, "median": statistics.median(rates),
+            "min": min(rates), "max": max(rates)}
+
+
+def hbm_roofline(name, kt, steps, bytes_per_elem_stage, elements, hbm, hbm_kind, traffic=None):
+    """Roofline of an HBM-bound kernel: algorithmic bytes of one launch (bytes per element-stage x
+    elements) over its average CUDA-event duration, against the measured copy bandwidth."""
+    avg_s = statistics.mean(kt[name]) * 1e-3
+    ach = bytes_per_elem_stage * elements / avg_s / 1e9
+    tot = {k: sum(v) for k, v in kt.items()}
+    return {"kernel": name, "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm,
+            "peak_kind": hbm_kind, "frac": ach / hbm, "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
+            "launches_per_step": len(kt[name]) // kernel_timed_steps(steps),
+            "share_of_step": tot[name] / sum(tot.values())}
+
+
+def alu_roofline(name, kt, steps, variant, elements, traffic=None):
+    """Roofline of an FP64-pipe-bound element kernel (algorithmic flops, Sec. 6.2 counting)."""
+    avg_s = statistics.mean(kt[name]) * 1e-3
+    if name == "element_update" and variant == 1:
+        flops = ALG_FLOPS_ELEMENT_P1 * elements
+    elif name == "element_update":
+        # fused and tiled variants evaluate the edge fluxes inside the element kernel
+        flops = (ALG_FLOPS_ELEMENT_P1 + 1.5 * ALG_FLOPS_EDGE_P1) * elements
+    elif name == "edge_flux":
+        flops = ALG_FLOPS_EDGE_P1 * 1.5 * elements
+    else:
+        flops = None
+    tot = {k: sum(v) for k, v in kt.items()}
+    ach = flops / avg_s / 1e9 if flops else None
+    return {"kernel": name, "bound": "alu", "unit": "GFLOP/s", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
+            "peak_kind": "derived from unit counts and clocks (FP64); the FMA probe measured 1,054 GFLOP/s",
+            "frac": ach / FP64_PEAK_GFLOPS if ach else None, "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
+            "launches_per_step": len(kt[name]) // kernel_timed_steps(steps),
+            "share_of_step": tot[name] / sum(tot.values())}
+
+
 def dominant(kt):
     tot = {k: sum(v) for k, v in kt.items()}
     name = max(tot, key=tot.get)
@@ -381,22 +425,7 @@ def main():
     hbm, hbm_kind = peaks()
     name, avg_s, tot = dominant(kt)
     ne = case.mesh.n_elems
-    if name == "element_update" and variant == 1:
-        flops = ALG_FLOPS_ELEMENT_P1 * ne
-    elif name == "element_update":
-        # fused and tiled variants evaluate the edge fluxes inside the element kernel
-        flops = (ALG_FLOPS_ELEMENT_P1 + 1.5 * ALG_FLOPS_EDGE_P1) * ne
-    elif name == "edge_flux":
-        flops = ALG_FLOPS_EDGE_P1 * 1.5 * ne
-    else:
-        flops = None
-    roof = {"kernel": name, "bound": "alu", "unit": "GFLOP/s",
-            "achieved": flops / avg_s / 1e9 if flops else None, "peak": FP64_PEAK_GFLOPS,
-            "peak_kind": "derived from unit counts and clocks (FP64)",
-            "frac": (flops / avg_s / 1e9) / FP64_PEAK_GFLOPS if flops else None,
-            "traffic": recorded_traffic(name, "fp64", ne, variant),
-            "avg_launch_ms": avg_s * 1e3, "launches_per_step": len(kt[name]) // kernel_timed_steps(args.steps),
-            "share_of_step": tot[name] / sum(tot.values())}
+    roof = alu_roofline(name, kt, args.steps, variant, ne, recorded_traffic(name, "fp64", ne, variant))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -408,6 +437,7 @@ def main():
             "hbm_gbs_algorithmic": ALG_BYTES[("fp64", 1)] * value / world / 1e9,
             "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
             "roofline": roof,
+            "runs": run_stats(ms, case.mesh.n_elems * 2),
             "kernel_ms_per_step": {k: sum(v) / kernel_timed_steps(args.steps) for k, v in kt.items()},
             "clocks": clk.summary()}
     if world == 1:
@@ -428,14 +458,22 @@ def extras(stream, flush, hbm):
                                ("fp32_mixed_p2", synth.config2(p=2, precision=synth.FP32_MIXED), "mixed", 2),
                                ("fp64_storm_3.2M", synth.config3(), "fp64", 1),
                                ("fp32_mixed_storm_3.2M", synth.config3(precision=synth.FP32_MIXED), "mixed", 1)):
-        m, ms, kt, (kps, variant, block) = run_form(case, 20, 3, stream, flush)
-        rate = case.mesh.n_elems * 2 * 20 / (sum(ms) * 1e-3)
+        steps = 20
+        m, ms, kt, (kps, variant, block) = run_form(case, steps, 3, stream, flush)
+        ne = case.mesh.n_elems
+        rate = ne * 2 * steps / (sum(ms) * 1e-3)
         name, avg_s, tot = dominant(kt)
         gbs = ALG_BYTES[(form, p)] * rate / 1e9
-        out[key] = {"value": rate, "unit": UNIT, "elements": case.mesh.n_elems, "ms_per_step": sum(ms) / 20,
+        hbm_kind = peaks()[1]
+        if form == "fp64":
+            roof = alu_roofline(name, kt, steps, variant, ne, recorded_traffic(name, form, ne, variant))
+        else:
+            roof = hbm_roofline("element_update", kt, steps, ALG_BYTES[(form, p)], ne, hbm, hbm_kind,
+                                recorded_traffic("element_update", form, ne, variant))
+        out[key] = {"value": rate, "unit": UNIT, "elements": ne, "ms_per_step": sum(ms) / steps,
                     "variant": variant, "block": block, "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm,
-                    "dominant_kernel": name,
-                    "kernel_ms_per_step": {k: sum(v) / kernel_timed_steps(20) for k, v in kt.items()}}
+                    "dominant_kernel": name, "roofline": roof, "runs": run_stats(ms, ne * 2),
+                    "kernel_ms_per_step": {k: sum(v) / kernel_timed_steps(steps) for k, v in kt.items()}}
         del m
     out["ensemble_64_storms"] = ensemble_form(stream)
     return out
@@ -454,12 +492,23 @@ def ensemble_form(stream, steps=10):
     ens.step(3)
     ens.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ens.step(steps)
-    e1.record(stream)
-    ens.sync()
-    ms = e0.elapsed_time(e1) / steps
+    run_ms = []
+    for _ in range(5):  # five runs of `steps` steps; the median is reported
+        e0.record(stream)
+        ens.step(steps)
+        e1.record(stream)
+        ens.sync()
+        run_ms.append(e0.elapsed_time(e1) / steps)
+    ms = statistics.median(run_ms)
     units = sum(meshes[mi].n_elems for mi, _, _ in members) * 2
+    # per-kernel times of one step (event nodes between the ensemble's launches)
+    ens.set_kernel_timing(True)
+    ens.step(1)
+    ens.sync()
+    kt = {}
+    for name, t in ens.kernel_times():
+        kt.setdefault(name, []).append(t)
+    ens.set_kernel_timing(False)
     del ens
     seq_ms = 0.0
     per_mesh = {}
@@ -477,8 +526,15 @@ def ensemble_form(stream, steps=10):
         per_mesh[mesh.n_elems] = t
         seq_ms += t * sum(1 for j, _, _ in members if j == mi)
         del m
+    hbm, hbm_kind = peaks()
+    ach = ALG_BYTES[("mixed", 1)] * units / (ms * 1e-3) / 1e9
+    roof = {"kernel": "the whole ensemble step (" + ("one persistent launch" if mode == 1 else "all phase launches") + ")",
+            "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm, "peak_kind": hbm_kind, "frac": ach / hbm,
+            "traffic": None, "avg_launch_ms": ms, "launches_per_step": kps}
     return {"value": units / (ms * 1e-3), "unit": UNIT, "members": len(members),
-            "elements_per_stage": units // 2, "ms_per_step": ms, "mode": "persistent" if mode == 1 else "phased",
+            "elements_per_stage": units // 2, "ms_per_step": ms, "ms_per_step_runs": run_ms,
+            "roofline": roof, "kernel_ms_one_step": {k: sum(v) for k, v in kt.items()},
+            "mode": "persistent" if mode == 1 else "phased",
             "block": block, "gpu_launches_per_step": kps, "l2": "working set ~4 GB > L2, no flush",
             "autotune_ms_per_step": tune,
             "fp64_sequential_ms_per_step": seq_ms, "fp64_single_ms_per_step_by_mesh": per_mesh,

@@ -534,105 +534,132 @@ __device__ __forceinline__ void elem_load(const DevMesh &m, const double *u, int
 }
 
 // Area integrals (Alg. 1): advective + pressure flux and friction, r_k set (not accumulated).
+// The weight w_q is folded into the velocities, U = w_q q_x / H and V = w_q q_y / H, and the
+// pressure term (g/2) zeta (zeta + 2 h_b) is summed without its factor g/2.  At P = 1 (grad phi
+// constant) the point sums are G = (Gx, Gy, Hy, Ps): sums of q_x U, q_x V, q_y V and
+// w_q zeta (zeta + 2 h_b); at P = 2 the points add to r directly.  fr: the friction integrals.
 template <int P, typename T>
-__device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph, T r[3][nd_of(P)],
-                                          const DevMesh &m, const int e) {
-  constexpr int ND = nd_of(P), NQA = nqa_of(P);
+struct AreaSums {
+  T G[4];
+  T fr[2][nd_of(P)];
+};
+
+// One area quadrature point's contributions (added to r at P = 2, to a otherwise).
+template <int P, typename T>
+__device__ __forceinline__ void area_point(const ElemCtx<P, T> &c, const Phys &ph, T r[3][nd_of(P)],
+                                           AreaSums<P, T> &a, const DevMesh &m, const int e, const int q) {
+  constexpr int ND = nd_of(P);
   const Tab<T> &tb = ctab<T>(P);
+  const T g = pc<T>(ph.g, ph.f.g);
+  const T rx = c.rx, ry = c.ry, sx = c.sx, sy = c.sy;
+  const T (&w)[3][ND] = c.w;
+  const T (&hb)[3] = c.hb;
+  const T hg = T(0.5) * g;
+  const T z = modal_value<ND, T>(w[0], tb.phq[q]);
+  const T qx = modal_value<ND, T>(w[1], tb.phq[q]);
+  const T qy = modal_value<ND, T>(w[2], tb.phq[q]);
+  // h_b at the point: read in the FP64 form (host-computed; an FP64 interpolation costs more
+  // issue than the load), interpolated in the latency-bound float form
+  T hq;
+  if constexpr (sizeof(T) == sizeof(double))
+    hq = ((const T *)m.hbq)[(size_t)q * m.ne + e];
+  else
+    hq = hb[0] * tb.nq[q][0] + hb[1] * tb.nq[q][1] + hb[2] * tb.nq[q][2];
+  const T H = z + hq;
+  const T wq = tb.wq[q];
+  const T iHw = wq * rcp_t(H);
+  const T U = qx * iHw, V = qy * iHw;
+  const T Pw = wq * (z * (z + T(2) * hq));
+  if constexpr (P == 1) {
+    a.G[0] += qx * U;
+    a.G[1] += qx * V;
+    a.G[2] += qy * V;
+    a.G[3] += Pw;
+  } else {
+    const T Pg = hg * Pw;
+    const T Fxx = qx * U + Pg, Fxy = qx * V, Fyy = qy * V + Pg;  // w_q F
+#pragma unroll
+    for (int k = 1; k < ND; ++k) {
+      const T gx = rx * tb.dxq[q][k] + sx * tb.dyq[q][k];
+      const T gy = ry * tb.dxq[q][k] + sy * tb.dyq[q][k];
+      r[0][k] += wq * (gx * qx + gy * qy);
+      r[1][k] += gx * Fxx + gy * Fxy;
+      r[2][k] += gx * Fxy + gy * Fyy;
+    }
+  }
+  if (ph.friction) {
+    // w_q tau_b q = c |q| q / H^2 w_q (times H^-1/3 for Manning) = c |U| U / w_q for H > 0;
+    // the sign of 1/w_q follows H so that the same holds for H < 0
+    T cq = pc<T>(ph.cf, ph.f.cf);
+    if (ph.friction == DGSWEM_FRICTION_MANNING) cq = pc<T>(ph.gn2, ph.f.gn2) * rcbrt(H);
+    else if (ph.friction != DGSWEM_FRICTION_QUADRATIC) cq = T(0);
+    const T Um = sqrt_t(U * U + V * V);
+    const T kq = cq * Um * (positive(H) ? tb.iwq[q] : -tb.iwq[q]);
+    const T tx = kq * U, ty = kq * V;
+    a.fr[0][0] += tx;  // psi_00 = 1
+    a.fr[1][0] += ty;
+#pragma unroll
+    for (int k = 1; k < ND; ++k) {
+      a.fr[0][k] += tx * tb.phq[q][k];
+      a.fr[1][k] += ty * tb.phq[q][k];
+    }
+  }
+}
+
+// The area integrals from the point sums: the P = 1 flux terms through the constant gradients,
+// the friction, and the factor |J|.
+template <int P, typename T>
+__device__ __forceinline__ void area_close(const ElemCtx<P, T> &c, const Phys &ph, T r[3][nd_of(P)],
+                                           AreaSums<P, T> &a) {
+  constexpr int ND = nd_of(P);
   const T g = pc<T>(ph.g, ph.f.g);
   const T rx = c.rx, ry = c.ry, sx = c.sx, sy = c.sy, dJ = c.dJ;
   const T (&w)[3][ND] = c.w;
-  const T (&hb)[3] = c.hb;
+  const T hg = T(0.5) * g;
+  if constexpr (P == 1) {
+    T &Gx = a.G[0], &Gy = a.G[1], &Hy = a.G[2], &Ps = a.G[3];
+    const T Pg = hg * Ps;
+    Gx += Pg;
+    Hy += Pg;
+    // grad psi_10 = J^-T (1, 1/2), grad psi_01 = J^-T (0, 3/2); the mass flux q is linear, so
+    // sum_q w_q q(x_q) = 2 q_00 exactly
+    const T g1x = rx + T(0.5) * sx, g1y = ry + T(0.5) * sy;
+    const T g2x = T(1.5) * sx, g2y = T(1.5) * sy;
+    r[0][1] = T(2) * (g1x * w[1][0] + g1y * w[2][0]);
+    r[0][2] = T(2) * (g2x * w[1][0] + g2y * w[2][0]);
+    r[1][1] = g1x * Gx + g1y * Gy;
+    r[1][2] = g2x * Gx + g2y * Gy;
+    r[2][1] = g1x * Gy + g1y * Hy;
+    r[2][2] = g2x * Gy + g2y * Hy;
+  }
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    r[0][k] *= dJ;
+    r[1][k] = (r[1][k] - a.fr[0][k]) * dJ;
+    r[2][k] = (r[2][k] - a.fr[1][k]) * dJ;
+  }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void area_zero(T r[3][nd_of(P)], AreaSums<P, T> &a) {
 #pragma unroll
   for (int v = 0; v < 3; ++v)
 #pragma unroll
-    for (int k = 0; k < ND; ++k) r[v][k] = T(0);
-  {
-    T fr[2][ND];
+    for (int k = 0; k < nd_of(P); ++k) r[v][k] = T(0);
 #pragma unroll
-    for (int k = 0; k < ND; ++k) fr[0][k] = fr[1][k] = T(0);
-    // The weight w_q is folded into the velocities, U = w_q q_x / H and V = w_q q_y / H, and the
-    // pressure term (g/2) zeta (zeta + 2 h_b) is summed without its factor g/2.  P = 1 (grad phi
-    // constant): Gx, Gy, Hy = sums of q_x U, q_x V, q_y V; Ps = sum of w_q zeta (zeta + 2 h_b).
-    T Gx = 0, Gy = 0, Hy = 0, Ps = 0;
-    const T hg = T(0.5) * g;
+  for (int i = 0; i < 4; ++i) a.G[i] = T(0);
 #pragma unroll
-    for (int q = 0; q < NQA; ++q) {
-      const T z = modal_value<ND, T>(w[0], tb.phq[q]);
-      const T qx = modal_value<ND, T>(w[1], tb.phq[q]);
-      const T qy = modal_value<ND, T>(w[2], tb.phq[q]);
-      // h_b at the point: read in the FP64 form (host-computed; an FP64 interpolation costs more
-      // issue than the load), interpolated in the latency-bound float form
-      T hq;
-      if constexpr (sizeof(T) == sizeof(double))
-        hq = ((const T *)m.hbq)[(size_t)q * m.ne + e];
-      else
-        hq = hb[0] * tb.nq[q][0] + hb[1] * tb.nq[q][1] + hb[2] * tb.nq[q][2];
-      const T H = z + hq;
-      const T wq = tb.wq[q];
-      const T iHw = wq * rcp_t(H);
-      const T U = qx * iHw, V = qy * iHw;
-      const T Pw = wq * (z * (z + T(2) * hq));
-      if constexpr (P == 1) {
-        Gx += qx * U;
-        Gy += qx * V;
-        Hy += qy * V;
-        Ps += Pw;
-      } else {
-        const T Pg = hg * Pw;
-        const T Fxx = qx * U + Pg, Fxy = qx * V, Fyy = qy * V + Pg;  // w_q F
-#pragma unroll
-        for (int k = 1; k < ND; ++k) {
-          const T gx = rx * tb.dxq[q][k] + sx * tb.dyq[q][k];
-          const T gy = ry * tb.dxq[q][k] + sy * tb.dyq[q][k];
-          r[0][k] += wq * (gx * qx + gy * qy);
-          r[1][k] += gx * Fxx + gy * Fxy;
-          r[2][k] += gx * Fxy + gy * Fyy;
-        }
-      }
-      if (ph.friction) {
-        // w_q tau_b q = c |q| q / H^2 w_q (times H^-1/3 for Manning) = c |U| U / w_q for H > 0;
-        // the sign of 1/w_q follows H so that the same holds for H < 0
-        T cq = pc<T>(ph.cf, ph.f.cf);
-        if (ph.friction == DGSWEM_FRICTION_MANNING) cq = pc<T>(ph.gn2, ph.f.gn2) * rcbrt(H);
-        else if (ph.friction != DGSWEM_FRICTION_QUADRATIC) cq = T(0);
-        const T Um = sqrt_t(U * U + V * V);
-        const T kq = cq * Um * (positive(H) ? tb.iwq[q] : -tb.iwq[q]);
-        const T tx = kq * U, ty = kq * V;
-        fr[0][0] += tx;  // psi_00 = 1
-        fr[1][0] += ty;
-#pragma unroll
-        for (int k = 1; k < ND; ++k) {
-          fr[0][k] += tx * tb.phq[q][k];
-          fr[1][k] += ty * tb.phq[q][k];
-        }
-      }
-    }
-    if constexpr (P == 1) {
-      const T Pg = hg * Ps;
-      Gx += Pg;
-      Hy += Pg;
-    }
-    if constexpr (P == 1) {
-      // grad psi_10 = J^-T (1, 1/2), grad psi_01 = J^-T (0, 3/2); the mass flux q is linear, so
-      // sum_q w_q q(x_q) = 2 q_00 exactly
-      const T g1x = rx + T(0.5) * sx, g1y = ry + T(0.5) * sy;
-      const T g2x = T(1.5) * sx, g2y = T(1.5) * sy;
-      r[0][1] = T(2) * (g1x * w[1][0] + g1y * w[2][0]);
-      r[0][2] = T(2) * (g2x * w[1][0] + g2y * w[2][0]);
-      r[1][1] = g1x * Gx + g1y * Gy;
-      r[1][2] = g2x * Gx + g2y * Gy;
-      r[2][1] = g1x * Gy + g1y * Hy;
-      r[2][2] = g2x * Gy + g2y * Hy;
-    }
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-      r[0][k] *= dJ;
-      r[1][k] = (r[1][k] - fr[0][k]) * dJ;
-      r[2][k] = (r[2][k] - fr[1][k]) * dJ;
-    }
-  }
+  for (int k = 0; k < nd_of(P); ++k) a.fr[0][k] = a.fr[1][k] = T(0);
+}
 
+template <int P, typename T>
+__device__ __forceinline__ void elem_area(const ElemCtx<P, T> &c, const Phys &ph, T r[3][nd_of(P)],
+                                          const DevMesh &m, const int e) {
+  AreaSums<P, T> a;
+  area_zero<P, T>(r, a);
+#pragma unroll
+  for (int q = 0; q < nqa_of(P); ++q) area_point<P, T>(c, ph, r, a, m, e, q);
+  area_close<P, T>(c, ph, r, a);
 }
 
 // Inverse mass matrix, closed-form linear sources and the RK stage; writes u^(s+1) and the means
@@ -933,38 +960,155 @@ __device__ __forceinline__ void element_body(const DevMesh &m, const StageArgs &
   elem_finish<P, T, MT>(m, s, ph, write_rhs, e, c, r);
 }
 
-template <int P>
-__device__ __forceinline__ void front_update_body(const DevMesh &m, const StageArgs &s, const Phys &ph,
-                                                  int write_rhs, int e) {
-  constexpr int ND = nd_of(P), NQE = nqe_of(P);
-  DevMesh md = m;
-  md.geo = m.geo_d;
-  md.lima = m.lima_d;
-  md.hbq = m.hbq_d;
-  StageArgs sd = s;
-  sd.cls = nullptr;
-  double phe[3][NQE][ND];
-  const Tab<double> &td = c_td[P - 1];
-#pragma unroll
-  for (int l = 0; l < 3; ++l)
-#pragma unroll
-    for (int q = 0; q < NQE; ++q)
-#pragma unroll
-      for (int k = 0; k < ND; ++k) phe[l][q][k] = td.phe[l][q][k];
-  // the means go to the float form's limiter copy (float) and to mean64
-  element_body<P, double, false, float>(md, sd, ph, write_rhs, e, phe);
-}
 // List entry i -> block i mod gridDim.x, lane i / gridDim.x: consecutive entries (neighbouring
 // front elements) go to different SMs, and an SM's few front elements share one warp, so the
 // double work of a short list spreads over the whole GPU instead of a few SMs' FP64 pipes.
 __device__ __forceinline__ unsigned front_entry0() { return blockIdx.x + gridDim.x * threadIdx.x; }
 __device__ __forceinline__ unsigned front_stride() { return gridDim.x * blockDim.x; }
 
-// The listed front elements of one model (flat index = element), one per thread.
+// Weighted numerical flux at Gauss point q of local edge l of element e (double, as element_body
+// computes it without the split variant's edge slots): hl w_q Fhat.n, n outward from e.
 template <int P>
-__global__ void __launch_bounds__(32) k_front(const DevMesh m, const StageArgs s, const Phys ph, const int write_rhs) {
+__device__ __forceinline__ void front_edge_point(const DevMesh &md, const StageArgs &s, const Phys &ph,
+                                                 const ElemCtx<P, double> &c, const int e, const int l, const int q,
+                                                 double f[3]) {
+  constexpr int ND = nd_of(P), NQE = nqe_of(P);
+  const Tab<double> &tb = c_td[P - 1];
+  const int ne = md.ne;
+  const double g = ph.g, sqg = ph.sqrt_g;
+  const double *geo = md.geo_d;
+  const int j = md.nbr[(size_t)l * ne + e];
+  const double hl = geo[(GEO_HL0 + l) * (size_t)ne + e];
+  const double nx = geo[(GEO_NX0 + l) * (size_t)ne + e], ny = geo[(GEO_NY0 + l) * (size_t)ne + e];
+  const double hbA = l == 0 ? c.hb[1] : (l == 1 ? c.hb[2] : c.hb[0]);
+  const double hbB = l == 0 ? c.hb[2] : (l == 1 ? c.hb[0] : c.hb[1]);
+  double wp[3];
+#pragma unroll
+  for (int v = 0; v < 3; ++v) wp[v] = modal_value<ND, double>(c.w[v], tb.phe[l][q]);
+  const double hbq = 0.5 * ((1.0 - tb.se[q]) * hbA + (1.0 + tb.se[q]) * hbB);
+  double F[3];
+  bool flows = false;
+  if (j >= 0) {
+    const int lj = (md.nle[e] >> (2 * l)) & 3;
+    flows = edge_flows<P>(ph, s.wd ? s.wd[e] : 0, s.wd ? s.wd[j] : 0, s.uin, ne, e, l, j, lj, hbA, hbB);
+    if (flows) {
+      double wm[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        double x = s.uin[(size_t)(v * ND) * ne + j];  // psi_00 = 1
+#pragma unroll
+        for (int k = 1; k < ND; ++k) x += s.uin[(size_t)(v * ND + k) * ne + j] * tb.phe[lj][NQE - 1 - q][k];
+        wm[v] = x;
+      }
+      numflux(ph, g, sqg, wp, wm, hbq, nx, ny, F);
+    }
+  }
+  if (j == NBR_RIVER) {
+    river(ph, g, sqg, wp, hbq, nx, ny, F);
+  } else if (j == NBR_OPEN) {
+    const double ts = stage_time(s.clk, s.tau, s.tide_t);
+    const double wo[3] = {ph.tide_amp * sin(ph.tide_omega * ts + ph.tide_phase), wp[1], wp[2]};
+    numflux(ph, g, sqg, wp, wo, hbq, nx, ny, F);
+  } else if (!flows) {  // land boundary, or an interior edge closed by wetting/drying
+    wall(ph, g, sqg, wp, hbq, nx, ny, F);
+  }
+  const double wgt = hl * tb.we[q];
+#pragma unroll
+  for (int v = 0; v < 3; ++v) f[v] = wgt * F[v];
+}
+
+// Sum over the `width` lanes of an aligned lane group (width a power of two, at most 32).
+template <int WIDTH>
+__device__ __forceinline__ double group_sum(double x) {
+#pragma unroll
+  for (int o = WIDTH / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// The double update of front elements by groups of lanes.  One thread's double update is a latency
+// chain of thousands of instructions on GB300's narrow FP64 pipe, and a warp instruction holds that
+// pipe for the same time whatever the number of active lanes; so each element gets a group of
+// LPE lanes (16 at p = 1: two elements per warp; 32 at p = 2): lane q < NQA of the group evaluates
+// area point q and lane LPE/2 + l NQE + q Gauss point q of local edge l, the group sums their
+// contributions, and its first lane closes the area integrals, adds the edge terms and applies the
+// inverse mass matrix, the closed-form sources and the RK stage (elem_finish).  Every lane of the
+// warp calls this (the sums shuffle across the whole warp); has: the group has an element.
+template <int P>
+__device__ __forceinline__ void front_update_group(const DevMesh &m, const StageArgs &s, const Phys &ph,
+                                                   const int write_rhs, const bool has, const int e) {
+  constexpr int ND = nd_of(P), NQA = nqa_of(P), NQE = nqe_of(P);
+  constexpr int LPE = P == 1 ? 16 : 32;
+  static_assert(NQA <= LPE / 2 && 3 * NQE <= LPE / 2, "lanes per element");
+  const int sub = threadIdx.x & (LPE - 1);
+  DevMesh md = m;
+  md.geo = m.geo_d;
+  md.lima = m.lima_d;
+  md.hbq = m.hbq_d;
+  ElemCtx<P, double> c;
+  double ra[3][ND], re[3][ND];
+  AreaSums<P, double> a;
+  area_zero<P, double>(ra, a);
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int k = 0; k < ND; ++k) re[v][k] = 0.0;
+  if (has) {
+    elem_load<P, double>(md, s.uin, e, c);
+    if (sub < NQA) {
+      area_point<P, double>(c, ph, ra, a, md, e, sub);
+    } else if (sub >= LPE / 2 && sub < LPE / 2 + 3 * NQE) {
+      const int l = (sub - LPE / 2) / NQE, q = (sub - LPE / 2) % NQE;
+      double f[3];
+      front_edge_point<P>(md, s, ph, c, e, l, q, f);
+      const Tab<double> &tb = c_td[P - 1];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        re[v][0] = -f[v];  // psi_00 = 1
+#pragma unroll
+        for (int k = 1; k < ND; ++k) re[v][k] = -(f[v] * tb.phe[l][q][k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      if constexpr (P == 2) ra[v][k] = group_sum<LPE>(ra[v][k]);  // at P = 1 the points add to a.G
+      re[v][k] = group_sum<LPE>(re[v][k]);
+    }
+  if constexpr (P == 1) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a.G[i] = group_sum<LPE>(a.G[i]);
+  }
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    a.fr[0][k] = group_sum<LPE>(a.fr[0][k]);
+    a.fr[1][k] = group_sum<LPE>(a.fr[1][k]);
+  }
+  if (has && sub == 0) {
+    area_close<P, double>(c, ph, ra, a);
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int k = 0; k < ND; ++k) ra[v][k] += re[v][k];
+    StageArgs sd = s;
+    sd.cls = nullptr;
+    elem_finish<P, double, float>(md, sd, ph, write_rhs, e, c, ra);
+  }
+}
+
+// The listed front elements of one model (flat index = element): 32 / LPE consecutive entries per
+// warp, warps of 128-thread blocks spread over the SMs.
+template <int P>
+__global__ void __launch_bounds__(128) k_front(const DevMesh m, const StageArgs s, const Phys ph, const int write_rhs) {
+  constexpr int EPW = P == 1 ? 2 : 1;  // elements per warp
   const unsigned n = *s.fcnt;
-  for (unsigned i = front_entry0(); i < n; i += front_stride()) front_update_body<P>(m, s, ph, write_rhs, s.flist[i]);
+  const unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned slot = (threadIdx.x & 31) / (32 / EPW);
+  for (unsigned i0 = w * EPW; i0 < n; i0 += nw * EPW) {  // the same trip count in every lane of a warp
+    const unsigned i = i0 + slot;
+    front_update_group<P>(m, s, ph, write_rhs, i < n, i < n ? s.flist[i] : 0);
+  }
 }
 
 // The float form's bounds keep the register counts these kernels had before the out-of-line front
@@ -1310,116 +1454,137 @@ __device__ __noinline__ void limiter_rebuild(const T d0, const T d1, const T d2,
   *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) * tb.lim_idet);
 }
 
+// Cockburn-Shu limiting of variable v of element e (see limwd_body); nb: the face neighbours, code:
+// the limiter's neighbour pairs (m.limj[e]).  Returns true when the linear modes were rebuilt.
+template <int P, typename T>
+__device__ __forceinline__ bool limit_variable(const DevMesh &m, double *u, const T *mean, const int e, const int v,
+                                               const int nb[3], const unsigned code, const uint8_t *fcls) {
+  constexpr int ND = nd_of(P);
+  const int ne = m.ne;
+  const Tab<T> &tb = ctab<T>(P);
+  const T nu = T(1.5);
+  const T *A = (const T *)m.lima;
+  const double d0 = u[(size_t)(v * ND) * ne + e];
+  const double d1 = u[(size_t)(v * ND + 1) * ne + e];
+  const double d2 = u[(size_t)(v * ND + 2) * ne + e];
+  T db3[3];  // neighbour means (stored in T: the float form rounds them once, when written)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (nb[j] < 0) {
+      db3[j] = from_d<T>(d0);
+    } else if (sizeof(T) == sizeof(double) && fcls && !fcls[nb[j]]) {
+      db3[j] = (T)u[(size_t)(v * ND) * ne + nb[j]];
+    } else {
+      db3[j] = mean[(size_t)v * ne + nb[j]];
+    }
+  }
+  if constexpr (sizeof(T) == sizeof(double)) {
+    // Filtered predicate (after Shewchuk's floating-point filters): a float evaluation with an
+    // error margin well above its rounding proves, when it can, that minmod returns the midpoint
+    // deviation at every edge, i.e. the limiter leaves this variable untouched; only the
+    // undecided cases run the exact double test below.  Zero slopes are untouched exactly.
+    if (((__double_as_longlong(d1) | __double_as_longlong(d2)) << 1) == 0) return false;  // both +-0
+    const float f0 = d2f(d0), f1 = d2f(d1), f2 = d2f(d2);
+    const Tab<float> &tf = ctab<float>(P);
+    bool sure = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float p1 = tf.phm[i][1], p2 = tf.phm[i][2];
+      const float ut = f1 * p1 + f2 * p2;
+      const float eu = 1e-6f * (fabsf(f1 * p1) + fabsf(f2 * p2));
+      const unsigned c = (code >> (4 * i)) & 15u;
+      const int j1 = c & 3, j2 = c >> 2;
+      float db = 0.f, ed = 0.f;
+      if (j1 != 3) {
+        const float a1 = d2f(A[(size_t)(2 * i) * ne + e]), a2 = d2f(A[(size_t)(2 * i + 1) * ne + e]);
+        const float b1 = d2f(db3[j1]), b2 = d2f(db3[j2]);
+        db = 1.5f * (a1 * (b1 - f0) + a2 * (b2 - f0));
+        ed = 1e-6f * 1.5f * (fabsf(a1) * (fabsf(b1) + fabsf(f0)) + fabsf(a2) * (fabsf(b2) + fabsf(f0))) + 1e-30f;
+      }
+      const bool ok = (fabsf(ut) > eu) && (fabsf(db) > ed) && ((ut > 0.f) == (db > 0.f)) &&
+                      (fabsf(ut) + eu < fabsf(db) - ed);
+      sure = sure && ok;
+    }
+    if (sure) return false;
+  }
+  const T u0 = from_d<T>(d0);
+  const T u1 = from_d<T>(d1);
+  const T u2 = from_d<T>(d2);
+  T dd[3];  // neighbour mean minus own mean
+#pragma unroll
+  for (int j = 0; j < 3; ++j) dd[j] = db3[j] - u0;
+  // midpoint deviations of the linear part; in double from the linear Dubiner modes at the
+  // edge midpoints, (1/2, 1/2), (-1/2, 1/2) and (0, -1) (Eq. dubiner): the same values as the
+  // table products (halving is exact), from two additions
+  T ut[3];
+  if constexpr (sizeof(T) == sizeof(double)) {
+    ut[0] = half_exact(u1 + u2);
+    ut[1] = half_exact(u2 - u1);
+    ut[2] = -u2;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ut[i] = u1 * tb.phm[i][1] + u2 * tb.phm[i][2];
+  }
+  T d[3];
+  bool act = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const unsigned c = (code >> (4 * i)) & 15u;
+    const int j1 = c & 3, j2 = c >> 2;
+    // select without dynamic register indexing (which would place dd in local memory)
+    const T x1 = j1 == 0 ? dd[0] : (j1 == 1 ? dd[1] : dd[2]);
+    const T x2 = j2 == 0 ? dd[0] : (j2 == 1 ? dd[1] : dd[2]);
+    T db = T(0);
+    if (j1 != 3) db = A[(size_t)(2 * i) * ne + e] * x1 + A[(size_t)(2 * i + 1) * ne + e] * x2;
+    d[i] = minmod(ut[i], nu * db);
+    act |= differs(d[i], ut[i]);
+  }
+  if (!act) return false;
+  limiter_rebuild<P, T>(d[0], d[1], d[2], u + (size_t)(v * ND + 1) * ne + e, u + (size_t)(v * ND + 2) * ne + e);
+  return true;
+}
+
 // fcls (float form, set when front elements exist): in the float path, skip the front elements
 // (cls 1: the front kernels limit them); in the double path of a front element, read a neighbour's
 // mean from `mean` (mean64) if it is at the front too, else from its updated state u (which the
 // float limiter, running after the front kernels, has not yet changed).
+template <int P, typename T>
+__device__ __forceinline__ void wetdry_elem(const DevMesh &m, double *u, uint8_t *wd, const Phys &ph, int *err,
+                                            int do_wd, const int e);
+
 template <int P, typename T>
 __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const T *mean, uint8_t *wd,
                                            const Phys &ph, int *err, int do_lim, int do_wd, const int e,
                                            const uint8_t *fcls = nullptr) {
   constexpr int ND = nd_of(P);
   const int ne = m.ne;
-  const Tab<T> &tb = ctab<T>(P);
   if constexpr (sizeof(T) == sizeof(float)) {
     if (fcls && fcls[e]) return;
   }
   if (do_lim) {
-    const T nu = T(1.5);
     int nb[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) nb[j] = m.nbr[(size_t)j * ne + e];
     const unsigned code = m.limj[e];
-    const T *A = (const T *)m.lima;
     bool any = false;
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      const double d0 = u[(size_t)(v * ND) * ne + e];
-      const double d1 = u[(size_t)(v * ND + 1) * ne + e];
-      const double d2 = u[(size_t)(v * ND + 2) * ne + e];
-      T db3[3];  // neighbour means (stored in T: the float form rounds them once, when written)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        if (nb[j] < 0) {
-          db3[j] = from_d<T>(d0);
-        } else if (sizeof(T) == sizeof(double) && fcls && !fcls[nb[j]]) {
-          db3[j] = (T)u[(size_t)(v * ND) * ne + nb[j]];
-        } else {
-          db3[j] = mean[(size_t)v * ne + nb[j]];
-        }
-      }
-      if constexpr (sizeof(T) == sizeof(double)) {
-        // Filtered predicate (after Shewchuk's floating-point filters): a float evaluation with an
-        // error margin well above its rounding proves, when it can, that minmod returns the midpoint
-        // deviation at every edge, i.e. the limiter leaves this variable untouched; only the
-        // undecided cases run the exact double test below.  Zero slopes are untouched exactly.
-        if (((__double_as_longlong(d1) | __double_as_longlong(d2)) << 1) == 0) continue;  // both +-0
-        const float f0 = d2f(d0), f1 = d2f(d1), f2 = d2f(d2);
-        const Tab<float> &tf = ctab<float>(P);
-        bool sure = true;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const float p1 = tf.phm[i][1], p2 = tf.phm[i][2];
-          const float ut = f1 * p1 + f2 * p2;
-          const float eu = 1e-6f * (fabsf(f1 * p1) + fabsf(f2 * p2));
-          const unsigned c = (code >> (4 * i)) & 15u;
-          const int j1 = c & 3, j2 = c >> 2;
-          float db = 0.f, ed = 0.f;
-          if (j1 != 3) {
-            const float a1 = d2f(A[(size_t)(2 * i) * ne + e]), a2 = d2f(A[(size_t)(2 * i + 1) * ne + e]);
-            const float b1 = d2f(db3[j1]), b2 = d2f(db3[j2]);
-            db = 1.5f * (a1 * (b1 - f0) + a2 * (b2 - f0));
-            ed = 1e-6f * 1.5f * (fabsf(a1) * (fabsf(b1) + fabsf(f0)) + fabsf(a2) * (fabsf(b2) + fabsf(f0))) + 1e-30f;
-          }
-          const bool ok = (fabsf(ut) > eu) && (fabsf(db) > ed) && ((ut > 0.f) == (db > 0.f)) &&
-                          (fabsf(ut) + eu < fabsf(db) - ed);
-          sure = sure && ok;
-        }
-        if (sure) continue;
-      }
-      const T u0 = from_d<T>(d0);
-      const T u1 = from_d<T>(d1);
-      const T u2 = from_d<T>(d2);
-      T dd[3];  // neighbour mean minus own mean
-#pragma unroll
-      for (int j = 0; j < 3; ++j) dd[j] = db3[j] - u0;
-      // midpoint deviations of the linear part; in double from the linear Dubiner modes at the
-      // edge midpoints, (1/2, 1/2), (-1/2, 1/2) and (0, -1) (Eq. dubiner): the same values as the
-      // table products (halving is exact), from two additions
-      T ut[3];
-      if constexpr (sizeof(T) == sizeof(double)) {
-        ut[0] = half_exact(u1 + u2);
-        ut[1] = half_exact(u2 - u1);
-        ut[2] = -u2;
-      } else {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) ut[i] = u1 * tb.phm[i][1] + u2 * tb.phm[i][2];
-      }
-      T d[3];
-      bool act = false;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const unsigned c = (code >> (4 * i)) & 15u;
-        const int j1 = c & 3, j2 = c >> 2;
-        // select without dynamic register indexing (which would place dd in local memory)
-        const T x1 = j1 == 0 ? dd[0] : (j1 == 1 ? dd[1] : dd[2]);
-        const T x2 = j2 == 0 ? dd[0] : (j2 == 1 ? dd[1] : dd[2]);
-        T db = T(0);
-        if (j1 != 3) db = A[(size_t)(2 * i) * ne + e] * x1 + A[(size_t)(2 * i + 1) * ne + e] * x2;
-        d[i] = minmod(ut[i], nu * db);
-        act |= differs(d[i], ut[i]);
-      }
-      if (!act) continue;
-      any = true;
-      limiter_rebuild<P, T>(d[0], d[1], d[2], u + (size_t)(v * ND + 1) * ne + e, u + (size_t)(v * ND + 2) * ne + e);
-    }
+    for (int v = 0; v < 3; ++v) any |= limit_variable<P, T>(m, u, mean, e, v, nb, code, fcls);
     if constexpr (P == 2) {
       if (any)
         for (int v = 0; v < 3; ++v)
           for (int k = 3; k < ND; ++k) u[(size_t)(v * ND + k) * ne + e] = 0.0;
     }
   }
-  if (do_wd) {  // 1: apply the operator, 2: classify only (flags from the current state)
+  if (do_wd) wetdry_elem<P, T>(m, u, wd, ph, err, do_wd, e);
+}
+
+// The wetting/drying operator on element e (see above); do_wd 1: apply, 2: classify only.
+template <int P, typename T>
+__device__ __forceinline__ void wetdry_elem(const DevMesh &m, double *u, uint8_t *wd, const Phys &ph, int *err,
+                                            int do_wd, const int e) {
+  constexpr int ND = nd_of(P);
+  const int ne = m.ne;
+  {  // do_wd 1: apply the operator, 2: classify only (flags from the current state)
     const bool write = do_wd == 1;
     const double h0 = ph.h0;
     const double z0 = u[e], z1 = u[(size_t)ne + e], z2 = u[2 * (size_t)ne + e];
@@ -1510,16 +1675,42 @@ __device__ __forceinline__ void front_limwd_body(const DevMesh &m, double *u, co
   md.lima = m.lima_d;
   limwd_body<P, double>(md, u, mean64, wd, ph, err, do_lim, do_wd, e, cls);
 }
-// The listed front elements of one model, one per thread (entries spread as in k_front).
+// The listed front elements of one model, four lanes each: lanes 0-2 of a group limit one variable
+// each (zeta, q_x, q_y), then lane 0 drops the quadratic modes of a limited element (p = 2) and
+// applies the wetting/drying operator; groups of eight elements per warp, blocks spread over the
+// SMs.
 template <int P>
-__global__ void __launch_bounds__(32) k_limwd_front(const DevMesh m, double *u, const double *mean64,
-                                                    const uint8_t *cls, uint8_t *wd, const Phys ph, int *err,
-                                                    int do_lim, int do_wd, const int *flist,
-                                                    const unsigned *fcnt) {
+__global__ void __launch_bounds__(128) k_limwd_front(const DevMesh m, double *u, const double *mean64,
+                                                     const uint8_t *cls, uint8_t *wd, const Phys ph, int *err,
+                                                     int do_lim, int do_wd, const int *flist,
+                                                     const unsigned *fcnt) {
+  constexpr int ND = nd_of(P);
   const unsigned n = *fcnt;
-  for (unsigned i = front_entry0(); i < n; i += front_stride()) {
-    const int e = flist[i];
-    if (e < m.nown) front_limwd_body<P>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, e);
+  const int lane = threadIdx.x & 31, sub = lane & 3;
+  const unsigned gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 2, ng = (gridDim.x * blockDim.x) >> 2;
+  DevMesh md = m;
+  md.lima = m.lima_d;
+  for (unsigned i0 = 0; i0 < n; i0 += ng) {  // the same trip count in every lane of a warp
+    const unsigned i = i0 + gid;
+    const int e = i < n ? flist[i] : -1;
+    const bool own = e >= 0 && e < m.nown;
+    bool acted = false;
+    if (own && do_lim && sub < 3) {
+      int nb[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) nb[j] = m.nbr[(size_t)j * m.ne + e];
+      acted = limit_variable<P, double>(md, u, mean64, e, sub, nb, m.limj[e], cls);
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, acted);
+    __syncwarp();  // the limited modes before the wet/dry lane reads them
+    if (own && sub == 0) {
+      if constexpr (P == 2) {
+        if ((b >> lane) & 7u)
+          for (int v = 0; v < 3; ++v)
+            for (int k = 3; k < ND; ++k) u[(size_t)(v * ND + k) * m.ne + e] = 0.0;
+      }
+      if (do_wd) wetdry_elem<P, double>(md, u, wd, ph, err, do_wd, e);
+    }
   }
 }
 
@@ -1636,18 +1827,26 @@ template <int P, typename T>
 __device__ __noinline__ void ens_front_phase(const EnsArgs &a, int phase, int stage, int t_begin, int t_step) {
   const unsigned n = *(volatile unsigned *)&a.fcnt[stage];
   const int B = blockDim.x;
-  // entry i -> block i mod t_step, thread i / t_step (spread over the SMs, as in k_front)
+  if (phase == 3) {  // lane groups per front element, as in k_front
+    constexpr int EPW = P == 1 ? 2 : 1;
+    const unsigned w = ((unsigned)t_begin * B + threadIdx.x) >> 5, nw = ((unsigned)t_step * B) >> 5;
+    const unsigned slot = (threadIdx.x & 31) / (32 / EPW);
+    for (unsigned i0 = w * EPW; i0 < n; i0 += nw * EPW) {
+      const unsigned i = i0 + slot;
+      const int id = i < n ? a.flist[i] : a.flist[i0];
+      const MemberDev &md = a.mem[a.etile[id / B]];
+      front_update_group<P>(md.m, member_stage<T>(md, a, stage), md.ph, 0, i < n, id - md.etile0 * B);
+    }
+    return;
+  }
+  // entry i -> block i mod t_step, thread i / t_step (spread over the SMs)
   for (unsigned i = t_begin + (unsigned)t_step * threadIdx.x; i < n; i += (unsigned)t_step * B) {
     const int id = a.flist[i];
     const MemberDev &md = a.mem[a.etile[id / B]];
     const int e = id - md.etile0 * B;
-    if (phase == 3) {
-      front_update_body<P>(md.m, member_stage<T>(md, a, stage), md.ph, 0, e);
-    } else {
-      double *in, *out;
-      stage_buffers(stage, a.nstages, md.U0, md.U1, md.U2, in, out);
-      front_limwd_body<P>(md.m, out, md.mean64, md.cls, md.wd, md.ph, a.err, md.ph.limiter, md.ph.wetdry, e);
-    }
+    double *in, *out;
+    stage_buffers(stage, a.nstages, md.U0, md.U1, md.U2, in, out);
+    front_limwd_body<P>(md.m, out, md.mean64, md.cls, md.wd, md.ph, a.err, md.ph.limiter, md.ph.wetdry, e);
   }
 }
 
@@ -1906,18 +2105,20 @@ inline int front_blocks() {
 }
 inline void launch_front_t(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, int write_rhs,
                            cudaStream_t st) {
+  // 8 blocks of 4 warps per SM: one warp per front element, up to 32 per SM at a time
   if (p == 1)
-    k_front<1><<<front_blocks(), 32, 0, st>>>(m, s, ph, write_rhs);
+    k_front<1><<<8 * front_blocks(), 128, 0, st>>>(m, s, ph, write_rhs);
   else
-    k_front<2><<<front_blocks(), 32, 0, st>>>(m, s, ph, write_rhs);
+    k_front<2><<<8 * front_blocks(), 128, 0, st>>>(m, s, ph, write_rhs);
 }
 inline void launch_limwd_front_t(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean64,
                                  const uint8_t *cls, uint8_t *wd, const Phys &ph, int *err, const int *flist,
                                  const unsigned *fcnt, cudaStream_t st) {
+  // 2 blocks of 32 four-lane groups per SM
   if (p == 1)
-    k_limwd_front<1><<<front_blocks(), 32, 0, st>>>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, flist, fcnt);
+    k_limwd_front<1><<<2 * front_blocks(), 128, 0, st>>>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, flist, fcnt);
   else
-    k_limwd_front<2><<<front_blocks(), 32, 0, st>>>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, flist, fcnt);
+    k_limwd_front<2><<<2 * front_blocks(), 128, 0, st>>>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, flist, fcnt);
 }
 
 }  // namespace dg
