@@ -54,6 +54,7 @@ struct EnsembleState {
   int block = 128, grid = 0, fault = 0, any_limwd = 0, any_inline = 0, any_front = 0;
   int *flist = nullptr;       // front list of all members (float form with wetting/drying)
   unsigned *fcnt = nullptr;   // its counter per stage
+  unsigned long long *work = nullptr;  // persistent launch: work-item claim counters
   unsigned long long timeout_ns = 1000000000ull;  // 1 s per grid-barrier wait
   std::vector<TuneEntry> tune;
 };
@@ -92,6 +93,7 @@ static void ens_layout(dgswem_ctx *c, char *base, size_t *bytes) {
   for (EnsMember &mb : E.mem) ne_all += E.meshes[mb.mesh].hm.ne;
   E.flist = k.take<int>(ne_all);
   E.fcnt = k.take<unsigned>(MAX_STAGES);
+  E.work = k.take<unsigned long long>(3 * MAX_STAGES);
   E.d_mem = k.take<MemberDev>(E.mem.size());
   E.d_etile = k.take<int>(E.max_etile);
   E.d_ntile = k.take<int>(E.max_ntile);
@@ -190,6 +192,7 @@ static int init_states(dgswem_ctx *c) {
   cudaMemsetAsync(c->step, 0, sizeof(long long), s);
   cudaMemsetAsync(E.bar, 0, 2 * sizeof(unsigned), s);
   cudaMemsetAsync(E.fcnt, 0, MAX_STAGES * sizeof(unsigned), s);
+  cudaMemsetAsync(E.work, 0, 3 * MAX_STAGES * sizeof(unsigned long long), s);
   if (int r = ctx_cuda(c, cudaStreamSynchronize(s), "ensemble init")) return r;
   return ctx_cuda(c, cudaGetLastError(), "ensemble init");
 }
@@ -227,6 +230,7 @@ void ensemble_enqueue_step(dgswem_ctx *c, std::vector<const char *> *names) {
   a.any_front = E.any_front;
   a.flist = E.flist;
   a.fcnt = E.fcnt;
+  a.work = E.work;
   a.timeout_ns = E.timeout_ns;
   if (names) {
     cudaEventRecordWithFlags(c->ev[0], c->st, cudaEventRecordExternal);

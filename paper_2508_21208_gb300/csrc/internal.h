@@ -219,6 +219,7 @@ struct EnsArgs {
   int any_front;           // some member has front elements to list (float form with wetting/drying)
   int *flist;              // the front list of every member (flat element indices: tile * block + i)
   unsigned *fcnt;          // its counter per stage
+  unsigned long long *work;  // persistent launch: work-item claim counters, [stage][phase 0, 1, 2]
   unsigned long long timeout_ns;
 };
 

@@ -1850,13 +1850,35 @@ __device__ __noinline__ void ens_front_phase(const EnsArgs &a, int phase, int st
   }
 }
 
+// Work items of a phase: statically t_begin, t_begin + t_step, ... (one per block in the phased
+// launches), or claimed dynamically from a counter (the persistent launch, where a static split
+// leaves some blocks with the slow items: storm-core tiles take longer).  The counter of each
+// (stage, phase) grows by n + gridDim.x per step (every block ends with one failed claim), so the
+// step's claims start at base = steps done x (n + gridDim.x).
+struct TileClaim {
+  unsigned long long *ctr;  // null: static
+  unsigned long long base;
+  int *s_t;                 // shared slot for the claimed index
+  int t_begin, t_step;
+  __device__ __forceinline__ int first(int n) const { return ctr ? next(n) : t_begin; }
+  __device__ __forceinline__ int next(int n, int t = 0) const {
+    if (!ctr) return t + t_step;
+    __syncthreads();  // every thread has read the previous index
+    if (threadIdx.x == 0) *s_t = (int)(atomicAdd(ctr, 1ull) - base);
+    __syncthreads();
+    return *s_t;
+  }
+};
+
 template <int P, typename T>
 __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage, int t_begin, int t_step,
                                           MemberDev *sd, const T (*s_phe)[nqe_of(P)][nd_of(P)],
-                                          unsigned char *smem_raw) {
+                                          unsigned char *smem_raw, const TileClaim *cl = nullptr) {
+  const TileClaim st{nullptr, 0, nullptr, t_begin, t_step};
+  const TileClaim &c = cl ? *cl : st;
   if (phase == 1) {  // element update, one shared-memory tile per work item
     if (a.any_front && blockIdx.x == 0 && threadIdx.x == 0) a.fcnt[(stage + a.nstages - 1) % a.nstages] = 0u;
-    for (int t = t_begin; t < a.n_etile; t += t_step) {
+    for (int t = c.first(a.n_etile); t < a.n_etile; t = c.next(a.n_etile, t)) {
       load_member(sd, &a.mem[a.etile[t]]);
       const StageArgs sa = member_stage<T>(*sd, a, stage);
       tile_body<P, T>(sd->m, sd->tl, sa, sd->ph, 0, t - sd->etile0, smem_raw, s_phe);
@@ -1868,7 +1890,7 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
     return;
   }
   if (phase == 0) {  // WIND at the nodes of members with a hurricane
-    for (int t = t_begin; t < a.n_ntile; t += t_step) {
+    for (int t = c.first(a.n_ntile); t < a.n_ntile; t = c.next(a.n_ntile, t)) {
       load_member(sd, &a.mem[a.ntile[t]]);
       const int n = (t - sd->ntile0) * blockDim.x + threadIdx.x;
       if (n < sd->m.nn)
@@ -1876,13 +1898,11 @@ __device__ __forceinline__ void ens_phase(const EnsArgs &a, int phase, int stage
                         (T *)sd->frc, n);
     }
   } else {
-    for (int t = t_begin; t < a.n_etile; t += t_step) {
+    for (int t = c.first(a.n_etile); t < a.n_etile; t = c.next(a.n_etile, t)) {
       load_member(sd, &a.mem[a.etile[t]]);
       const int e = (t - sd->etile0) * blockDim.x + threadIdx.x;
       if (e >= sd->m.ne) continue;
-      if (phase == 1) {
-        continue;  // handled by the tiled loop below
-      } else if (sd->ph.limiter || sd->ph.wetdry) {
+      if (sd->ph.limiter || sd->ph.wetdry) {
         double *in, *out;
         stage_buffers(stage, a.nstages, sd->U0, sd->U1, sd->U2, in, out);
         limwd_body<P, T>(sd->m, out, static_cast<const T *>(sd->mean), sd->wd, sd->ph, a.err, sd->ph.limiter,
@@ -1903,14 +1923,22 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 5 : 2) : 1)) 
   __shared__ MemberDev sd;
   load_phe<P, T>(s_phe);
   __syncthreads();
+  __shared__ int s_t;
   if (*(volatile int *)a.err & ERR_TIMEOUT) return;  // an earlier step already failed
   const bool skip = a.fault && blockIdx.x == gridDim.x - 1;
+  // steps done, read by every block before the first grid barrier (block 0 bumps it after the last)
+  const unsigned long long done = (unsigned long long)*(volatile long long *)a.step;
+  auto claim = [&](int stage, int k, int n) {
+    return TileClaim{a.work + stage * 3 + k, done * (unsigned long long)(n + gridDim.x), &s_t, 0, 0};
+  };
   for (int stage = 0; stage < a.nstages; ++stage) {
     if (a.n_ntile > 0) {
-      ens_phase<P, T>(a, 0, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
+      const TileClaim c0 = claim(stage, 0, a.n_ntile);
+      ens_phase<P, T>(a, 0, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw, &c0);
       if (!grid_barrier(a, skip)) return;
     }
-    ens_phase<P, T>(a, 1, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
+    const TileClaim c1 = claim(stage, 1, a.n_etile);
+    ens_phase<P, T>(a, 1, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw, &c1);
     if (!grid_barrier(a, skip)) return;
     if (a.any_front) {  // front elements: double update, then double limiter and wet/dry
       ens_phase<P, T>(a, 3, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
@@ -1919,7 +1947,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 5 : 2) : 1)) 
       if (!grid_barrier(a, skip)) return;
     }
     if (a.any_limwd) {
-      ens_phase<P, T>(a, 2, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
+      const TileClaim c2 = claim(stage, 2, a.n_etile);
+      ens_phase<P, T>(a, 2, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw, &c2);
       if (stage < a.nstages - 1 && !grid_barrier(a, skip)) return;
     }
   }

@@ -389,3 +389,48 @@ def test_limiter_pair_order_worked_example():
     for order in (((0, 1), (1, 2), (2, 0)), ((1, 2), (2, 0), (0, 1))):
         alt, _ = _limit_from_geometry(mesh.xy, mesh.tri, u, order=order)
         assert np.allclose(alt[0, 1:3, 0], [0.0, 0.0], atol=1e-14)
+
+
+def test_wetdry_edge_rule_keeps_a_dry_bank_dry_while_water_sloshes():
+    """The edge rule in motion: water moving in a wet element against a dry bank element.
+
+    The shared edge runs from A (bed at the datum) to B (bed 1 m above it); the wet element W
+    below it deepens to 5.5 m at its third vertex, and the dry bank D above it rises to 2 m, with
+    its water at h0.  W's surface starts tilted up towards B (0.5 m at A, 1.05 m at B: wet
+    everywhere) and then sloshes back.  At the edge's Gauss points W's surface stays below the
+    edge's highest bed (1 m), so the edge is closed: D must stay exactly as it is and W must keep
+    its water, while W's water moves.  Letting every edge flow (removing the rule, planted in a
+    scratch copy of the oracle) moves water into D in the first step, since W's surface at the
+    edge lies well above D's (h0 above the bed)."""
+    xy = np.array([[0.0, 0.0], [1000.0, 0.0], [500.0, -1000.0], [500.0, 1000.0]])
+    tri = np.array([[0, 2, 1], [0, 1, 3]], np.int32)  # W = (A, E, B), D = (A, B, C)
+    bedge = np.array([[0, 2], [2, 1], [1, 3], [3, 0]], np.int32)
+    mesh = synth.Mesh(xy, tri, bedge, np.zeros(4, np.int32))
+    hb = np.array([0.0, -1.0, 5.0, -2.0])       # h_b positive down: bed elevations 0, 1, -5, 2 m
+    prm = synth.default_params(h0=0.01)
+    u = np.zeros((3, 3, 2))
+    u[0, :, 0] = _modes_from_vertices(0.5, 0.5, 1.05)           # W at its vertices A, E, B
+    u[0, :, 1] = _modes_from_vertices(*(0.01 - hb[[0, 1, 3]]))  # D at h0 depth
+    o = oracle.Oracle(mesh, hb, prm, init_modal=u)
+    o.set_state(u)
+    assert list(o.flags()) == [0, 2]
+    area = 0.5 * 1000.0 * 1000.0
+    d0 = o.state()[:, :, 1].copy()
+    w_mass = o.state()[0, 0, 0] * area
+    s, _ = oracle.edge_rule(2)
+    bed_top = 1.0
+    moved, w_flags = 0.0, set()
+    for _ in range(40):
+        z = o.state()[0, :, 0]
+        zA, zB = z[0] - z[1] - z[2], z[0] + 2.0 * z[2]  # W's surface at A and B (vertices 0 and 2)
+        traces = zA + (zB - zA) * 0.5 * (1.0 + s)
+        assert traces.max() < bed_top                  # the edge stays closed
+        o.step(1)
+        st = o.state()
+        assert np.array_equal(st[:, :, 1], d0)          # the bank is untouched
+        f = o.flags()
+        assert f[1] == 2 and f[0] in (0, 1)            # W may dry at B as it sloshes back
+        w_flags.add(int(f[0]))
+        assert abs(st[0, 0, 0] * area - w_mass) <= 1e-12 * w_mass
+        moved = max(moved, np.abs(st[1:, 0, 0]).max())
+    assert moved > 1e-3                                 # W's water does move
