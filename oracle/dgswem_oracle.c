@@ -487,20 +487,23 @@ static void wind(orc *o, double t) {
 
 /* ------------------------------------------------- point physics (Eq. SWE) */
 static double friction_tau(const orc_params *P, double qx, double qy, double H) {
+  if (!(H > 0.0)) return 0.0; /* no water: zero velocity (see flux_n) */
   double qm = sqrt(qx * qx + qy * qy);
   if (P->friction == 1) return P->g * P->manning_n * P->manning_n * qm / pow(H, 7.0 / 3.0);
   if (P->friction == 2) return P->cf * qm / (H * H);
   return 0.0;
 }
 
-/* normal component F(w).n of the physical flux; w = (zeta, qx, qy) */
+/* normal component F(w).n of the physical flux; w = (zeta, qx, qy).  The velocity q/H is taken
+ * as zero where the total depth H is not positive (no water there; the paper's equations divide
+ * by H without a rule for it), here, in the wave speeds and in the area integrals and friction. */
 static void flux_n(double g, const double w[3], double hb, double nx, double ny, double F[3]) {
   double H = w[0] + hb;
   double qn = w[1] * nx + w[2] * ny;
   double P = 0.5 * g * w[0] * (w[0] + 2.0 * hb);
   F[0] = qn;
-  F[1] = w[1] * qn / H + P * nx;
-  F[2] = w[2] * qn / H + P * ny;
+  F[1] = H > 0.0 ? w[1] * qn / H + P * nx : P * nx;
+  F[2] = H > 0.0 ? w[2] * qn / H + P * ny : P * ny;
 }
 
 /* local Lax-Friedrichs flux, n pointing from the inner (wi) to the outer (wo) state */
@@ -510,8 +513,8 @@ static void llf(double g, const double wi[3], const double wo[3], double hb, dou
   flux_n(g, wi, hb, nx, ny, Fi);
   flux_n(g, wo, hb, nx, ny, Fo);
   double Hi = wi[0] + hb, Ho = wo[0] + hb;
-  double si = fabs((wi[1] * nx + wi[2] * ny) / Hi) + sqrt(g * (Hi > 0.0 ? Hi : 0.0));
-  double so = fabs((wo[1] * nx + wo[2] * ny) / Ho) + sqrt(g * (Ho > 0.0 ? Ho : 0.0));
+  double si = Hi > 0.0 ? fabs((wi[1] * nx + wi[2] * ny) / Hi) + sqrt(g * Hi) : 0.0;
+  double so = Ho > 0.0 ? fabs((wo[1] * nx + wo[2] * ny) / Ho) + sqrt(g * Ho) : 0.0;
   double lam = si > so ? si : so;
   for (int v = 0; v < 3; ++v) out[v] = 0.5 * (Fi[v] + Fo[v]) - 0.5 * lam * (wo[v] - wi[v]);
 }
@@ -620,8 +623,13 @@ static void area_integrals(orc *o, int irk) {
       double Pp = 0.5 * P->g * ze * (ze + 2.0 * hbq);
       /* Continuity_Flux, X_Flux, Y_Flux */
       double Fx = qx, Fy = qy;
-      double Gx = qx * qx / H + Pp, Gy = qx * qy / H;
-      double Hx = qx * qy / H, Hy = qy * qy / H + Pp;
+      double Gx = Pp, Gy = 0.0, Hx = 0.0, Hy = Pp; /* zero velocity where H <= 0 (see flux_n) */
+      if (H > 0.0) {
+        Gx = qx * qx / H + Pp;
+        Gy = qx * qy / H;
+        Hx = qx * qy / H;
+        Hy = qy * qy / H + Pp;
+      }
       /* Continuity_Source, X_Source, Y_Source */
       double SR = P->rain_rate;
       double tau = friction_tau(P, qx, qy, H);

@@ -176,7 +176,8 @@ __device__ __forceinline__ T modal_value(const T (&w)[ND], const T *ph) {
 // Normal flux F(w).n of Eq. SWE with the pressure term (g/2)(H^2 - h_b^2) = (g/2) zeta (zeta + 2 h_b).
 // One side of an edge point: q.n, u.n = q.n / H, the wave speed |u.n| + sqrt(g H) and the pressure
 // term P = (g/2) zeta (zeta + 2 h_b), so that F(w).n = (q.n, q_x u.n + P n_x, q_y u.n + P n_y).
-// 1/H and sqrt(g H) come from one reciprocal square root; H <= 0 falls back to a plain divide.
+// 1/H and sqrt(g H) come from one reciprocal square root; where H <= 0 (no water) the velocity
+// and the wave speed are zero, in both fluxes, the area integrals and the friction.
 template <typename T>
 struct Side {
   T qn, un, s, P;
@@ -191,8 +192,8 @@ __device__ __forceinline__ Side<T> side_flux(T g, T sqrt_g, const T w[3], T hb, 
     const T rs = rsqrt_t(H);
     r.un = r.qn * rs * rs;
     c = sqrt_g * H * rs;
-  } else {
-    r.un = r.qn / H;
+  } else {  // no water: zero velocity and wave speed
+    r.un = T(0);
     c = T(0);
   }
   r.P = T(0.5) * g * w[0] * (w[0] + T(2) * hb);
@@ -567,7 +568,7 @@ __device__ __forceinline__ void area_point(const ElemCtx<P, T> &c, const Phys &p
     hq = hb[0] * tb.nq[q][0] + hb[1] * tb.nq[q][1] + hb[2] * tb.nq[q][2];
   const T H = z + hq;
   const T wq = tb.wq[q];
-  const T iHw = wq * rcp_t(H);
+  const T iHw = positive(H) ? wq * rcp_t(H) : T(0);  // zero velocity where there is no water
   const T U = qx * iHw, V = qy * iHw;
   const T Pw = wq * (z * (z + T(2) * hq));
   if constexpr (P == 1) {
@@ -588,13 +589,13 @@ __device__ __forceinline__ void area_point(const ElemCtx<P, T> &c, const Phys &p
     }
   }
   if (ph.friction) {
-    // w_q tau_b q = c |q| q / H^2 w_q (times H^-1/3 for Manning) = c |U| U / w_q for H > 0;
-    // the sign of 1/w_q follows H so that the same holds for H < 0
+    // w_q tau_b q = c |q| q / H^2 w_q (times H^-1/3 for Manning) = c |U| U / w_q for H > 0, and
+    // zero for H <= 0 (U = V = 0 there)
     T cq = pc<T>(ph.cf, ph.f.cf);
-    if (ph.friction == DGSWEM_FRICTION_MANNING) cq = pc<T>(ph.gn2, ph.f.gn2) * rcbrt(H);
+    if (ph.friction == DGSWEM_FRICTION_MANNING) cq = positive(H) ? pc<T>(ph.gn2, ph.f.gn2) * rcbrt(H) : T(0);
     else if (ph.friction != DGSWEM_FRICTION_QUADRATIC) cq = T(0);
     const T Um = sqrt_t(U * U + V * V);
-    const T kq = cq * Um * (positive(H) ? tb.iwq[q] : -tb.iwq[q]);
+    const T kq = cq * Um * tb.iwq[q];
     const T tx = kq * U, ty = kq * V;
     a.fr[0][0] += tx;  // psi_00 = 1
     a.fr[1][0] += ty;
@@ -1025,20 +1026,26 @@ __device__ __forceinline__ double group_sum(double x) {
   return x;
 }
 
+// Lanes per front element in the double update: a power of two at least as large as the number of
+// area points (NQA) and of edge Gauss points (3 NQE), which are equal at p = 1 (6) and p = 2 (12).
+template <int P>
+__host__ __device__ constexpr int front_lanes() { return P == 1 ? 8 : 16; }
+
 // The double update of front elements by groups of lanes.  One thread's double update is a latency
 // chain of thousands of instructions on GB300's narrow FP64 pipe, and a warp instruction holds that
 // pipe for the same time whatever the number of active lanes; so each element gets a group of
-// LPE lanes (16 at p = 1: two elements per warp; 32 at p = 2): lane q < NQA of the group evaluates
-// area point q and lane LPE/2 + l NQE + q Gauss point q of local edge l, the group sums their
-// contributions, and its first lane closes the area integrals, adds the edge terms and applies the
-// inverse mass matrix, the closed-form sources and the RK stage (elem_finish).  Every lane of the
-// warp calls this (the sums shuffle across the whole warp); has: the group has an element.
+// LPE = front_lanes lanes (four elements per warp at p = 1, two at p = 2), and lane j < NQA of a
+// group evaluates both area point j and edge Gauss point j (local edge j / NQE, point j % NQE):
+// no lane waits while another kind of point is computed.  The group sums the contributions, and
+// its first lane closes the area integrals, adds the edge terms and applies the inverse mass
+// matrix, the closed-form sources and the RK stage (elem_finish).  Every lane of the warp calls
+// this (the sums shuffle across the whole warp); has: the group has an element.
 template <int P>
 __device__ __forceinline__ void front_update_group(const DevMesh &m, const StageArgs &s, const Phys &ph,
                                                    const int write_rhs, const bool has, const int e) {
   constexpr int ND = nd_of(P), NQA = nqa_of(P), NQE = nqe_of(P);
-  constexpr int LPE = P == 1 ? 16 : 32;
-  static_assert(NQA <= LPE / 2 && 3 * NQE <= LPE / 2, "lanes per element");
+  constexpr int LPE = front_lanes<P>();
+  static_assert(NQA == 3 * NQE && NQA <= LPE, "one area point and one edge point per lane");
   const int sub = threadIdx.x & (LPE - 1);
   DevMesh md = m;
   md.geo = m.geo_d;
@@ -1056,8 +1063,7 @@ __device__ __forceinline__ void front_update_group(const DevMesh &m, const Stage
     elem_load<P, double>(md, s.uin, e, c);
     if (sub < NQA) {
       area_point<P, double>(c, ph, ra, a, md, e, sub);
-    } else if (sub >= LPE / 2 && sub < LPE / 2 + 3 * NQE) {
-      const int l = (sub - LPE / 2) / NQE, q = (sub - LPE / 2) % NQE;
+      const int l = sub / NQE, q = sub % NQE;
       double f[3];
       front_edge_point<P>(md, s, ph, c, e, l, q, f);
       const Tab<double> &tb = c_td[P - 1];
@@ -1098,13 +1104,14 @@ __device__ __forceinline__ void front_update_group(const DevMesh &m, const Stage
 }
 
 // The listed front elements of one model (flat index = element): 32 / LPE consecutive entries per
-// warp, warps of 128-thread blocks spread over the SMs.
+// warp; warp w of the list is warp w / gridDim.x of block w % gridDim.x, so that a short list
+// spreads over every SM (one busy warp per block) instead of filling the first blocks.
 template <int P>
 __global__ void __launch_bounds__(128) k_front(const DevMesh m, const StageArgs s, const Phys ph, const int write_rhs) {
-  constexpr int EPW = P == 1 ? 2 : 1;  // elements per warp
+  constexpr int EPW = 32 / front_lanes<P>();  // elements per warp
   const unsigned n = *s.fcnt;
-  const unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  const unsigned slot = (threadIdx.x & 31) / (32 / EPW);
+  const unsigned w = blockIdx.x + gridDim.x * (threadIdx.x >> 5), nw = gridDim.x * (blockDim.x >> 5);
+  const unsigned slot = (threadIdx.x & 31) / front_lanes<P>();
   for (unsigned i0 = w * EPW; i0 < n; i0 += nw * EPW) {  // the same trip count in every lane of a warp
     const unsigned i = i0 + slot;
     front_update_group<P>(m, s, ph, write_rhs, i < n, i < n ? s.flist[i] : 0);
@@ -1677,8 +1684,8 @@ __device__ __forceinline__ void front_limwd_body(const DevMesh &m, double *u, co
 }
 // The listed front elements of one model, four lanes each: lanes 0-2 of a group limit one variable
 // each (zeta, q_x, q_y), then lane 0 drops the quadratic modes of a limited element (p = 2) and
-// applies the wetting/drying operator; groups of eight elements per warp, blocks spread over the
-// SMs.
+// applies the wetting/drying operator.  Group g of the list is group g / gridDim.x of block
+// g % gridDim.x: a short list spreads over every SM, a few elements per busy warp.
 template <int P>
 __global__ void __launch_bounds__(128) k_limwd_front(const DevMesh m, double *u, const double *mean64,
                                                      const uint8_t *cls, uint8_t *wd, const Phys ph, int *err,
@@ -1687,7 +1694,7 @@ __global__ void __launch_bounds__(128) k_limwd_front(const DevMesh m, double *u,
   constexpr int ND = nd_of(P);
   const unsigned n = *fcnt;
   const int lane = threadIdx.x & 31, sub = lane & 3;
-  const unsigned gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 2, ng = (gridDim.x * blockDim.x) >> 2;
+  const unsigned gid = blockIdx.x + gridDim.x * (threadIdx.x >> 2), ng = (gridDim.x * blockDim.x) >> 2;
   DevMesh md = m;
   md.lima = m.lima_d;
   for (unsigned i0 = 0; i0 < n; i0 += ng) {  // the same trip count in every lane of a warp
@@ -1828,9 +1835,9 @@ __device__ __noinline__ void ens_front_phase(const EnsArgs &a, int phase, int st
   const unsigned n = *(volatile unsigned *)&a.fcnt[stage];
   const int B = blockDim.x;
   if (phase == 3) {  // lane groups per front element, as in k_front
-    constexpr int EPW = P == 1 ? 2 : 1;
-    const unsigned w = ((unsigned)t_begin * B + threadIdx.x) >> 5, nw = ((unsigned)t_step * B) >> 5;
-    const unsigned slot = (threadIdx.x & 31) / (32 / EPW);
+    constexpr int EPW = 32 / front_lanes<P>();
+    const unsigned w = (unsigned)t_begin + (unsigned)t_step * (threadIdx.x >> 5), nw = ((unsigned)t_step * B) >> 5;
+    const unsigned slot = (threadIdx.x & 31) / front_lanes<P>();
     for (unsigned i0 = w * EPW; i0 < n; i0 += nw * EPW) {
       const unsigned i = i0 + slot;
       const int id = i < n ? a.flist[i] : a.flist[i0];
@@ -2134,7 +2141,7 @@ inline int front_blocks() {
 }
 inline void launch_front_t(int p, const DevMesh &m, const StageArgs &s, const Phys &ph, int write_rhs,
                            cudaStream_t st) {
-  // 8 blocks of 4 warps per SM: one warp per front element, up to 32 per SM at a time
+  // 8 blocks of 4 warps per SM; the busy warps (32 / LPE list entries each) go one per block first
   if (p == 1)
     k_front<1><<<8 * front_blocks(), 128, 0, st>>>(m, s, ph, write_rhs);
   else
@@ -2143,7 +2150,7 @@ inline void launch_front_t(int p, const DevMesh &m, const StageArgs &s, const Ph
 inline void launch_limwd_front_t(int p, bool do_lim, int do_wd, const DevMesh &m, double *u, const double *mean64,
                                  const uint8_t *cls, uint8_t *wd, const Phys &ph, int *err, const int *flist,
                                  const unsigned *fcnt, cudaStream_t st) {
-  // 2 blocks of 32 four-lane groups per SM
+  // 2 blocks of 32 four-lane groups per SM; the list's groups go one per block first
   if (p == 1)
     k_limwd_front<1><<<2 * front_blocks(), 128, 0, st>>>(m, u, mean64, cls, wd, ph, err, do_lim, do_wd, flist, fcnt);
   else
