@@ -35,6 +35,9 @@
  *   - h_b is given at nodes and linear in each element; forcing is nodal and
  *     linear in each element;
  *   - friction tau_b = g n^2 |q| / H^(7/3) (Manning) or C_f |q| / H^2 (quadratic);
+ *   - where the total depth H is not positive (no water), the velocity q/H, the wave speed and
+ *     the friction are zero in the fluxes and the area integrals (the equations divide by H and
+ *     give no rule there); the pressure term stays;
  *   - SSP Runge-Kutta (Sec. 2.2: Shu-Osher SSPRK; the paper's production scheme is a DG-optimised
  *     SSPRK(s,q), Kubatko et al. 2014) in the two-register Shu-Osher form
  *     u^(i) = a_i u^n + b_i u^(i-1) + c_i dt L(u^(i-1)): SSP(2,2) (default) and SSP(3,3)
@@ -49,9 +52,10 @@
  *     shifted so that the mean normal discharge of the two traces is the inflow -q_in;
  *   - rain R (Eq. SWE): a uniform rate in the continuity equation;
  *   - hurricane: Holland (1980) pressure and gradient wind, Garratt (1977) drag.
- * Partly pinned: slope limiter (invariants, a hand-worked example and a recomputation from the
- * mesh geometry) and wet/dry (invariants, hand-worked examples and convergence to Thacker's
- * moving-shoreline solution in a parabolic bowl).
+ * Readings pinned by their own cases: slope limiter (invariants, hand-worked examples of the
+ * limiting and of the neighbour-pair order, and a recomputation from the mesh geometry) and
+ * wet/dry (invariants, hand-worked examples, the edge rule against a sloshing wet element, and
+ * convergence to Thacker's moving-shoreline solution in a parabolic bowl).
  *
  * Compile: gcc -O2 -ffp-contract=off -fPIC -shared (optionally -fopenmp).
  */
