@@ -1073,30 +1073,46 @@ __device__ __forceinline__ void front_update_group(const DevMesh &m, const Stage
 #pragma unroll
         for (int k = 1; k < ND; ++k) re[v][k] = -(f[v] * tb.phe[l][q][k]);
       }
+      if constexpr (P == 2) {
+        // area_close scales (r - friction) by |J| and the edge terms are added after it: fold
+        // both into this lane's r (edge terms divided by |J|), so that one array is summed
+        const double idJ = rcp_d(c.dJ);
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+          ra[0][k] = fma(re[0][k], idJ, ra[0][k]);
+          ra[1][k] = fma(re[1][k], idJ, ra[1][k] - a.fr[0][k]);
+          ra[2][k] = fma(re[2][k], idJ, ra[2][k] - a.fr[1][k]);
+          a.fr[0][k] = a.fr[1][k] = 0.0;
+        }
+      }
     }
   }
-#pragma unroll
-  for (int v = 0; v < 3; ++v)
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-      if constexpr (P == 2) ra[v][k] = group_sum<LPE>(ra[v][k]);  // at P = 1 the points add to a.G
-      re[v][k] = group_sum<LPE>(re[v][k]);
-    }
-  if constexpr (P == 1) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a.G[i] = group_sum<LPE>(a.G[i]);
-  }
-#pragma unroll
-  for (int k = 0; k < ND; ++k) {
-    a.fr[0][k] = group_sum<LPE>(a.fr[0][k]);
-    a.fr[1][k] = group_sum<LPE>(a.fr[1][k]);
-  }
-  if (has && sub == 0) {
-    area_close<P, double>(c, ph, ra, a);
+  if constexpr (P == 2) {
 #pragma unroll
     for (int v = 0; v < 3; ++v)
 #pragma unroll
-      for (int k = 0; k < ND; ++k) ra[v][k] += re[v][k];
+      for (int k = 0; k < ND; ++k) ra[v][k] = group_sum<LPE>(ra[v][k]);
+  } else {  // at P = 1 the area points add to a.G
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int k = 0; k < ND; ++k) re[v][k] = group_sum<LPE>(re[v][k]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a.G[i] = group_sum<LPE>(a.G[i]);
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      a.fr[0][k] = group_sum<LPE>(a.fr[0][k]);
+      a.fr[1][k] = group_sum<LPE>(a.fr[1][k]);
+    }
+  }
+  if (has && sub == 0) {
+    area_close<P, double>(c, ph, ra, a);
+    if constexpr (P == 1) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int k = 0; k < ND; ++k) ra[v][k] += re[v][k];
+    }
     StageArgs sd = s;
     sd.cls = nullptr;
     elem_finish<P, double, float>(md, sd, ph, write_rhs, e, c, ra);
@@ -1463,7 +1479,7 @@ __device__ __noinline__ void limiter_rebuild(const T d0, const T d1, const T d2,
 
 // Cockburn-Shu limiting of variable v of element e (see limwd_body); nb: the face neighbours, code:
 // the limiter's neighbour pairs (m.limj[e]).  Returns true when the linear modes were rebuilt.
-template <int P, typename T>
+template <int P, typename T, bool FILTER = true>
 __device__ __forceinline__ bool limit_variable(const DevMesh &m, double *u, const T *mean, const int e, const int v,
                                                const int nb[3], const unsigned code, const uint8_t *fcls) {
   constexpr int ND = nd_of(P);
@@ -1485,7 +1501,7 @@ __device__ __forceinline__ bool limit_variable(const DevMesh &m, double *u, cons
       db3[j] = mean[(size_t)v * ne + nb[j]];
     }
   }
-  if constexpr (sizeof(T) == sizeof(double)) {
+  if constexpr (sizeof(T) == sizeof(double) && FILTER) {
     // Filtered predicate (after Shewchuk's floating-point filters): a float evaluation with an
     // error margin well above its rounding proves, when it can, that minmod returns the midpoint
     // deviation at every edge, i.e. the limiter leaves this variable untouched; only the
@@ -1555,11 +1571,14 @@ __device__ __forceinline__ bool limit_variable(const DevMesh &m, double *u, cons
 // (cls 1: the front kernels limit them); in the double path of a front element, read a neighbour's
 // mean from `mean` (mean64) if it is at the front too, else from its updated state u (which the
 // float limiter, running after the front kernels, has not yet changed).
-template <int P, typename T>
+template <int P, typename T, bool FILTER = true>
 __device__ __forceinline__ void wetdry_elem(const DevMesh &m, double *u, uint8_t *wd, const Phys &ph, int *err,
                                             int do_wd, const int e);
 
-template <int P, typename T>
+// FILTER: decide the clear cases with float filters first (the bulk kernels); the front path,
+// whose elements are rarely clear cases and whose FP64 pipe is otherwise idle, goes straight to
+// the exact double tests (same results, a shorter dependency chain).
+template <int P, typename T, bool FILTER = true>
 __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const T *mean, uint8_t *wd,
                                            const Phys &ph, int *err, int do_lim, int do_wd, const int e,
                                            const uint8_t *fcls = nullptr) {
@@ -1575,18 +1594,18 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const T 
     const unsigned code = m.limj[e];
     bool any = false;
 #pragma unroll
-    for (int v = 0; v < 3; ++v) any |= limit_variable<P, T>(m, u, mean, e, v, nb, code, fcls);
+    for (int v = 0; v < 3; ++v) any |= limit_variable<P, T, FILTER>(m, u, mean, e, v, nb, code, fcls);
     if constexpr (P == 2) {
       if (any)
         for (int v = 0; v < 3; ++v)
           for (int k = 3; k < ND; ++k) u[(size_t)(v * ND + k) * ne + e] = 0.0;
     }
   }
-  if (do_wd) wetdry_elem<P, T>(m, u, wd, ph, err, do_wd, e);
+  if (do_wd) wetdry_elem<P, T, FILTER>(m, u, wd, ph, err, do_wd, e);
 }
 
 // The wetting/drying operator on element e (see above); do_wd 1: apply, 2: classify only.
-template <int P, typename T>
+template <int P, typename T, bool FILTER>
 __device__ __forceinline__ void wetdry_elem(const DevMesh &m, double *u, uint8_t *wd, const Phys &ph, int *err,
                                             int do_wd, const int e) {
   constexpr int ND = nd_of(P);
@@ -1595,7 +1614,7 @@ __device__ __forceinline__ void wetdry_elem(const DevMesh &m, double *u, uint8_t
     const bool write = do_wd == 1;
     const double h0 = ph.h0;
     const double z0 = u[e], z1 = u[(size_t)ne + e], z2 = u[2 * (size_t)ne + e];
-    {
+    if constexpr (FILTER) {
       // Filtered predicate: a float evaluation decides the clearly wet elements (every vertex depth
       // exceeds h0 by far more than the float rounding of its terms), for which the double test
       // below would change nothing; only the rest are tested in double.
@@ -1680,7 +1699,7 @@ __device__ __forceinline__ void front_limwd_body(const DevMesh &m, double *u, co
                                                  int do_lim, int do_wd, int e) {
   DevMesh md = m;
   md.lima = m.lima_d;
-  limwd_body<P, double>(md, u, mean64, wd, ph, err, do_lim, do_wd, e, cls);
+  limwd_body<P, double, false>(md, u, mean64, wd, ph, err, do_lim, do_wd, e, cls);
 }
 // The listed front elements of one model, four lanes each: lanes 0-2 of a group limit one variable
 // each (zeta, q_x, q_y), then lane 0 drops the quadratic modes of a limited element (p = 2) and
@@ -1706,7 +1725,7 @@ __global__ void __launch_bounds__(128) k_limwd_front(const DevMesh m, double *u,
       int nb[3];
 #pragma unroll
       for (int j = 0; j < 3; ++j) nb[j] = m.nbr[(size_t)j * m.ne + e];
-      acted = limit_variable<P, double>(md, u, mean64, e, sub, nb, m.limj[e], cls);
+      acted = limit_variable<P, double, false>(md, u, mean64, e, sub, nb, m.limj[e], cls);
     }
     const unsigned b = __ballot_sync(0xffffffffu, acted);
     __syncwarp();  // the limited modes before the wet/dry lane reads them
@@ -1716,7 +1735,7 @@ __global__ void __launch_bounds__(128) k_limwd_front(const DevMesh m, double *u,
           for (int v = 0; v < 3; ++v)
             for (int k = 3; k < ND; ++k) u[(size_t)(v * ND + k) * m.ne + e] = 0.0;
       }
-      if (do_wd) wetdry_elem<P, double>(md, u, wd, ph, err, do_wd, e);
+      if (do_wd) wetdry_elem<P, double, false>(md, u, wd, ph, err, do_wd, e);
     }
   }
 }
