@@ -104,16 +104,17 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, form: str, elements: int, variant: int):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels."""
-    p = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
-    if not os.path.exists(p):
+def recorded_traffic(kernel: str, form: str, elements: int, variant, p: int = 1):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels
+    (same kernel, form, variant and degree p)."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+    if not os.path.exists(path):
         return None
     sha = kernel_source_sha()
-    for line in open(p):
+    for line in open(path):
         kv = dict(re.findall(r"(\w+)=(\S+)", line))
         if (kv.get("kernel") == kernel and kv.get("form") == form and kv.get("src_sha") == sha
-                and kv.get("variant") in ("*", str(variant))):
+                and kv.get("variant") in ("*", str(variant)) and kv.get("p", "1") == str(p)):
             # captured on a larger mesh (DRAM-resident); traffic per launch scales with elements
             return float(kv["bytes"]) / float(kv["elements"]) * elements
     return None
@@ -466,10 +467,10 @@ def extras(stream, flush, hbm):
         gbs = ALG_BYTES[(form, p)] * rate / 1e9
         hbm_kind = peaks()[1]
         if form == "fp64":
-            roof = alu_roofline(name, kt, steps, variant, ne, recorded_traffic(name, form, ne, variant))
+            roof = alu_roofline(name, kt, steps, variant, ne, recorded_traffic(name, form, ne, variant, p))
         else:
             roof = hbm_roofline("element_update", kt, steps, ALG_BYTES[(form, p)], ne, hbm, hbm_kind,
-                                recorded_traffic("element_update", form, ne, variant))
+                                recorded_traffic("element_update", form, ne, variant, p))
         out[key] = {"value": rate, "unit": UNIT, "elements": ne, "ms_per_step": sum(ms) / steps,
                     "variant": variant, "block": block, "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm,
                     "dominant_kernel": name, "roofline": roof, "runs": run_stats(ms, ne * 2),
@@ -530,7 +531,8 @@ def ensemble_form(stream, steps=10):
     ach = ALG_BYTES[("mixed", 1)] * units / (ms * 1e-3) / 1e9
     roof = {"kernel": "the whole ensemble step (" + ("one persistent launch" if mode == 1 else "all phase launches") + ")",
             "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm, "peak_kind": hbm_kind, "frac": ach / hbm,
-            "traffic": None, "avg_launch_ms": ms, "launches_per_step": kps}
+            "traffic": recorded_traffic("ensemble_step", "mixed", units // 2, "persistent" if mode == 1 else "phased"),
+            "avg_launch_ms": ms, "launches_per_step": kps}
     return {"value": units / (ms * 1e-3), "unit": UNIT, "members": len(members),
             "elements_per_stage": units // 2, "ms_per_step": ms, "ms_per_step_runs": run_ms,
             "roofline": roof, "kernel_ms_one_step": {k: sum(v) for k, v in kt.items()},
