@@ -188,13 +188,19 @@ def test_mixed_precision_error_bound(variant, p):
     """FP32-mixed shelf with a moving shoreline (tide, dry land, limiter) against the FP64 oracle
     after 300 steps: surface elevation within 1e-4 m and discharge within 1e-3 m^2/s at every
     element vertex, identical wet/dry flags (the elements at the wetting/drying front take the
-    double path), and the water volume within 1e-11 of the oracle's."""
+    double path), and the water volume within float rounding of the volume the tide moved.
+
+    Interior edges conserve volume exactly in both forms (each edge's flux leaves one element and
+    enters the other), so the two volumes part only through the open boundary's fluxes, which the
+    mixed form evaluates in float (relative rounding ~6e-8 per value).  The bound is 1e-6 of the
+    net volume that crossed the boundary, which a leak inside the domain would exceed."""
     c = synth.config2(n=48, p=p, precision=synth.FP32_MIXED)
     g = Model(c.mesh, c.bathy, c.params, init_nodal=c.init_nodal, variant=variant, block=128)
     prm = dict(c.params)
     prm["precision"] = synth.FP64
     o = oracle.Oracle(c.mesh, c.bathy, prm, init_nodal=c.init_nodal, omp=True)
     assert g.dt == pytest.approx(o.dt, rel=1e-14)
+    v0 = o.mass()[1]
     g.step(300)
     o.step(300)
     fa, fb = g.flags(), o.flags()
@@ -204,7 +210,10 @@ def test_mixed_precision_error_bound(variant, p):
     assert np.abs(va[0] - vb[0]).max() <= 1e-4   # surface elevation, metres
     assert np.abs(va[1:] - vb[1:]).max() <= 1e-3  # discharge, m^2/s
     ma, mb = g.mass(), o.mass()
-    assert abs(ma[1] - mb[1]) <= 1e-11 * mb[1]
+    exchanged = abs(mb[1] - v0)
+    assert exchanged > 1e6  # the tide moved water through the open boundary
+    print(f"volume: mixed - FP64 = {ma[1] - mb[1]:.3g} m^3, exchanged {exchanged:.3g} m^3")
+    assert abs(ma[1] - mb[1]) <= 1e-6 * exchanged
 
 
 def test_mixed_precision_storm_error_bound():
