@@ -97,3 +97,28 @@ def test_fp64_one_storm_per_standard_mesh_matches_oracle():
         for v in range(3):
             rel = np.linalg.norm(a[v] - b[v]) / max(np.linalg.norm(b[v]), 1e-300)
             assert rel <= 1e-12, (i, v, rel)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("mode", [ENSEMBLE_PERSISTENT, ENSEMBLE_PHASED])
+def test_members_with_wetdry_fronts_equal_single_runs(mode, p):
+    """Shelf scenarios with dry land and a tide (FP32-mixed): the ensemble updates and limits its
+    wetting/drying front elements in double in its own front phases, and every member must equal
+    the same scenario run alone (whose front goes through the model's front kernels) bit for bit,
+    flags included."""
+    cases = [synth.config2(n=24, p=p, precision=synth.FP32_MIXED),
+             synth.config2(n=28, seed=5, p=p, precision=synth.FP32_MIXED)]
+    meshes = [c.mesh for c in cases]
+    bathys = [c.bathy for c in cases]
+    members = [(0, cases[0].params, cases[0].init_nodal), (1, cases[1].params, cases[1].init_nodal),
+               (0, dict(cases[0].params, tide_amp=0.3, tide_phase=1.0), cases[0].init_nodal)]
+    ens = Ensemble(meshes, bathys, members, block=64, mode=mode)
+    ens.step(40)
+    for i, (mi, prm, init) in enumerate(members):
+        single = Model(meshes[mi], bathys[mi], prm, init_nodal=init, variant=VARIANT_TILED, block=64)
+        single.step(40)
+        f = single.flags()
+        assert (f == 1).any() and (f == 0).any() and (f == 2).any()  # a front exists
+        assert np.array_equal(ens.flags(i), f), i
+        a, b = ens.state(i), single.state()
+        assert np.array_equal(a, b), (i, np.abs(a - b).max())
