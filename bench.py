@@ -104,9 +104,10 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, form: str, elements: int, variant, p: int = 1):
+def recorded_traffic(kernel: str, form: str, elements: int, variant, p: int = 1, scale: bool = False):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels
-    (same kernel, form, variant and degree p)."""
+    (same kernel, form, variant and degree p) and on a mesh of the same size; with scale, on any
+    mesh, scaled per element (the ensemble: its capture is a smaller batch of the same meshes)."""
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if not os.path.exists(path):
         return None
@@ -114,8 +115,8 @@ def recorded_traffic(kernel: str, form: str, elements: int, variant, p: int = 1)
     for line in open(path):
         kv = dict(re.findall(r"(\w+)=(\S+)", line))
         if (kv.get("kernel") == kernel and kv.get("form") == form and kv.get("src_sha") == sha
-                and kv.get("variant") in ("*", str(variant)) and kv.get("p", "1") == str(p)):
-            # captured on a larger mesh (DRAM-resident); traffic per launch scales with elements
+                and kv.get("variant") in ("*", str(variant)) and kv.get("p", "1") == str(p)
+                and (scale or int(kv["elements"]) == elements)):
             return float(kv["bytes"]) / float(kv["elements"]) * elements
     return None
 
@@ -531,7 +532,8 @@ def ensemble_form(stream, steps=10):
     ach = ALG_BYTES[("mixed", 1)] * units / (ms * 1e-3) / 1e9
     roof = {"kernel": "the whole ensemble step (" + ("one persistent launch" if mode == 1 else "all phase launches") + ")",
             "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": hbm, "peak_kind": hbm_kind, "frac": ach / hbm,
-            "traffic": recorded_traffic("ensemble_step", "mixed", units // 2, "persistent" if mode == 1 else "phased"),
+            "traffic": recorded_traffic("ensemble_step", "mixed", units // 2, "persistent" if mode == 1 else "phased",
+                                        scale=True),
             "avg_launch_ms": ms, "launches_per_step": kps}
     return {"value": units / (ms * 1e-3), "unit": UNIT, "members": len(members),
             "elements_per_stage": units // 2, "ms_per_step": ms, "ms_per_step_runs": run_ms,
