@@ -1514,16 +1514,26 @@ __device__ __noinline__ void limiter_rebuild(const T d0, const T d1, const T d2,
   *u2 = to_d<T>((tb.phm[0][1] * dh[1] - dh[0] * tb.phm[1][1]) * tb.lim_idet);
 }
 
+// The limiter's six decomposition weights of element e (rows of m.lima), loaded once for the three
+// variables (the limiter writes the state through a pointer, so the compiler could not reuse them).
+template <typename T>
+__device__ __forceinline__ void limiter_weights(const DevMesh &m, const int e, T A[6]) {
+  const T *L = (const T *)m.lima;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) A[r] = L[(size_t)r * m.ne + e];
+}
+
 // Cockburn-Shu limiting of variable v of element e (see limwd_body); nb: the face neighbours, code:
-// the limiter's neighbour pairs (m.limj[e]).  Returns true when the linear modes were rebuilt.
+// the limiter's neighbour pairs (m.limj[e]), A: its weights (limiter_weights).  Returns true when
+// the linear modes were rebuilt.
 template <int P, typename T, bool FILTER = true>
 __device__ __forceinline__ bool limit_variable(const DevMesh &m, double *u, const T *mean, const int e, const int v,
-                                               const int nb[3], const unsigned code, const uint8_t *fcls) {
+                                               const int nb[3], const unsigned code, const uint8_t *fcls,
+                                               const T A[6]) {
   constexpr int ND = nd_of(P);
   const int ne = m.ne;
   const Tab<T> &tb = ctab<T>(P);
   const T nu = T(1.5);
-  const T *A = (const T *)m.lima;
   const double d0 = u[(size_t)(v * ND) * ne + e];
   const double d1 = u[(size_t)(v * ND + 1) * ne + e];
   const double d2 = u[(size_t)(v * ND + 2) * ne + e];
@@ -1556,7 +1566,7 @@ __device__ __forceinline__ bool limit_variable(const DevMesh &m, double *u, cons
       const int j1 = c & 3, j2 = c >> 2;
       float db = 0.f, ed = 0.f;
       if (j1 != 3) {
-        const float a1 = d2f(A[(size_t)(2 * i) * ne + e]), a2 = d2f(A[(size_t)(2 * i + 1) * ne + e]);
+        const float a1 = d2f(A[2 * i]), a2 = d2f(A[2 * i + 1]);
         const float b1 = d2f(db3[j1]), b2 = d2f(db3[j2]);
         db = 1.5f * (a1 * (b1 - f0) + a2 * (b2 - f0));
         ed = 1e-6f * 1.5f * (fabsf(a1) * (fabsf(b1) + fabsf(f0)) + fabsf(a2) * (fabsf(b2) + fabsf(f0))) + 1e-30f;
@@ -1595,7 +1605,7 @@ __device__ __forceinline__ bool limit_variable(const DevMesh &m, double *u, cons
     const T x1 = j1 == 0 ? dd[0] : (j1 == 1 ? dd[1] : dd[2]);
     const T x2 = j2 == 0 ? dd[0] : (j2 == 1 ? dd[1] : dd[2]);
     T db = T(0);
-    if (j1 != 3) db = A[(size_t)(2 * i) * ne + e] * x1 + A[(size_t)(2 * i + 1) * ne + e] * x2;
+    if (j1 != 3) db = A[2 * i] * x1 + A[2 * i + 1] * x2;
     d[i] = minmod(ut[i], nu * db);
     act |= differs(d[i], ut[i]);
   }
@@ -1629,9 +1639,11 @@ __device__ __forceinline__ void limwd_body(const DevMesh &m, double *u, const T 
 #pragma unroll
     for (int j = 0; j < 3; ++j) nb[j] = m.nbr[(size_t)j * ne + e];
     const unsigned code = m.limj[e];
+    T A[6];
+    limiter_weights<T>(m, e, A);
     bool any = false;
 #pragma unroll
-    for (int v = 0; v < 3; ++v) any |= limit_variable<P, T, FILTER>(m, u, mean, e, v, nb, code, fcls);
+    for (int v = 0; v < 3; ++v) any |= limit_variable<P, T, FILTER>(m, u, mean, e, v, nb, code, fcls, A);
     if constexpr (P == 2) {
       if (any)
         for (int v = 0; v < 3; ++v)
@@ -1762,7 +1774,9 @@ __global__ void __launch_bounds__(128) k_limwd_front(const DevMesh m, double *u,
       int nb[3];
 #pragma unroll
       for (int j = 0; j < 3; ++j) nb[j] = m.nbr[(size_t)j * m.ne + e];
-      acted = limit_variable<P, double, false>(md, u, mean64, e, sub, nb, m.limj[e], cls);
+      double A[6];
+      limiter_weights<double>(md, e, A);
+      acted = limit_variable<P, double, false>(md, u, mean64, e, sub, nb, m.limj[e], cls, A);
     }
     const unsigned b = __ballot_sync(0xffffffffu, acted);
     __syncwarp();  // the limited modes before the wet/dry lane reads them
@@ -1777,9 +1791,11 @@ __global__ void __launch_bounds__(128) k_limwd_front(const DevMesh m, double *u,
   }
 }
 
-// float form: held to 64 registers (4 resident 256-thread blocks per SM), as without the front path
+// float form: held to 40 registers (6 resident 256-thread blocks per SM): the pass is bound by the
+// latency of its gathers, and more resident warps measured faster despite a small spill (storm
+// limiter 0.286 -> 0.241 ms per step against 56 registers)
 template <int P, typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_limwd(const DevMesh m, double *u, const T *mean,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) k_limwd(const DevMesh m, double *u, const T *mean,
                                                uint8_t *wd, const Phys ph, int *err, int do_lim,
                                                int do_wd, const uint8_t *cls) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
