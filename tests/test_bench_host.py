@@ -21,10 +21,13 @@ def test_recorded_traffic_needs_the_current_sources(tmp_path, monkeypatch):
     ])
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: sha)
-    assert bench.recorded_traffic("element_update", "fp64", 2000, 3) == 600000   # scaled per element
+    assert bench.recorded_traffic("element_update", "fp64", 1000, 3) == 300000   # the captured mesh
+    assert bench.recorded_traffic("element_update", "fp64", 2000, 3) is None     # another mesh size
+    assert bench.recorded_traffic("element_update", "fp64", 2000, 3, scale=True) == 600000  # per element
+    assert bench.recorded_traffic("element_update", "fp64", 1000, 3, p=2) is None  # another degree
     assert bench.recorded_traffic("element_update", "fp64", 1000, 1) is None     # stale sources
     assert bench.recorded_traffic("element_update", "mixed", 1000, 3) is None    # other form
-    assert bench.recorded_traffic("limiter_wetdry", "mixed", 1000, 4) == 50000   # any variant
+    assert bench.recorded_traffic("limiter_wetdry", "mixed", 2000, 4) == 100000  # any variant
     assert bench.recorded_traffic("edge_flux", "fp64", 1000, 1) is None
 
 
