@@ -196,9 +196,9 @@ void carve_mesh(Carver &k, const HostMesh &H, int p, bool mixed, DevMesh &m, int
   m.edle = k.take<uint8_t>(nint);
   m.edgeo = k.take<char>(tsz * 3 * nint);
   m.edhb = k.take<double>(2 * (size_t)nint);
-  // h_b at quadrature points: read by the FP64 form only
+  // h_b at quadrature points: the area points for the FP64 form, the edge Gauss points for both
   m.hbq = mixed ? nullptr : k.take<char>(tsz * nqa_of(p) * ne);
-  m.edhbq = mixed ? nullptr : k.take<char>(tsz * nqe_of(p) * nint);
+  m.edhbq = k.take<char>(tsz * nqe_of(p) * nint);
   m.nodexy = k.take<double>(2 * (size_t)nn);
   m.elf = mixed ? k.take<float>(9 * (size_t)ne) : nullptr;
   // the float form's double statics for the elements at the wetting/drying front
@@ -246,7 +246,7 @@ static void layout(dgswem_ctx *c, char *base, size_t *bytes) {
   T.code = k.take<uint8_t>(mt);
   T.geo = k.take<char>(tsz * 3 * mt);
   T.hb = k.take<double>(2 * (size_t)mt);
-  T.hbq = c->mixed ? nullptr : k.take<char>(tsz * NQE * mt);
+  T.hbq = k.take<char>(tsz * NQE * mt);
   *bytes = k.off;
 }
 

@@ -73,7 +73,7 @@ static void ens_layout(dgswem_ctx *c, char *base, size_t *bytes) {
     m.dt.code = k.take<uint8_t>(mt);
     m.dt.geo = k.take<char>(tsz * 3 * mt);
     m.dt.hb = k.take<double>(2 * (size_t)mt);
-    m.dt.hbq = c->mixed ? nullptr : k.take<char>(tsz * nqe_of(c->P) * mt);
+    m.dt.hbq = k.take<char>(tsz * nqe_of(c->P) * mt);
   }
   size_t stage = 0;
   for (EnsMember &mb : E.mem) {

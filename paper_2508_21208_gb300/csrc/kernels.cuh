@@ -472,9 +472,11 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
   const int code = m.edle[d], lp = code & 3, lm = code >> 2;
   const T *eg = (const T *)m.edgeo;
   const T nx = eg[d], ny = eg[nint + d], hl = eg[2 * nint + d];
-  const double hbA = m.edhb[d], hbB = m.edhb[nint + d];
-  const bool flows = edge_flows<P>(ph, s.wd ? s.wd[ep] : 0, s.wd ? s.wd[em] : 0, s.uin, ne, ep, lp,
-                                   em, lm, hbA, hbB);
+  const uint8_t fp = s.wd ? s.wd[ep] : 0, fm = s.wd ? s.wd[em] : 0;
+  // the edge's vertex depths decide only an edge with exactly one dry side
+  const bool one_dry = (fp == 2) != (fm == 2);
+  const double hbA = one_dry ? m.edhb[d] : 0.0, hbB = one_dry ? m.edhb[nint + d] : 0.0;
+  const bool flows = edge_flows<P>(ph, fp, fm, s.uin, ne, ep, lp, em, lm, hbA, hbB);
   s.emode[d] = flows ? 1 : 0;
   if (!flows) return;
   T wp[3][ND], wm[3][ND];
@@ -490,11 +492,7 @@ __global__ void __launch_bounds__(256) k_edge(const DevMesh m, const StageArgs s
       a[v] = modal_value<ND, T>(wp[v], s_phe[lp][q]);
       b[v] = modal_value<ND, T>(wm[v], s_phe[lm][NQE - 1 - q]);
     }
-    T hb;  // h_b at the point (as in the area integrals: read in FP64, interpolated in float)
-    if constexpr (sizeof(T) == sizeof(double))
-      hb = ((const T *)m.edhbq)[(size_t)q * nint + d];
-    else
-      hb = T(0.5) * ((T(1) - tb.se[q]) * from_d<T>(hbA) + (T(1) + tb.se[q]) * from_d<T>(hbB));
+    const T hb = ((const T *)m.edhbq)[(size_t)q * nint + d];  // h_b at the point, host-computed
     T f[3];
     numflux(ph, g, sqg, a, b, hb, nx, ny, f);
     const T wgt = hl * tb.we[q];
@@ -533,7 +531,10 @@ __device__ __forceinline__ void elem_load_geom(const DevMesh &m, int e, ElemCtx<
   c.hbd[0] = m.hbv[e];
   c.hbd[1] = m.hbv[ne + e];
   c.hbd[2] = m.hbv[2 * (size_t)ne + e];
-  for (int a = 0; a < 3; ++a) c.hb[a] = from_d<T>(c.hbd[a]);
+  for (int a = 0; a < 3; ++a) {  // the float form's copies are rounded on the host like from_d
+    if constexpr (sizeof(T) == sizeof(float)) c.hb[a] = m.elf[(size_t)a * ne + e];
+    else c.hb[a] = c.hbd[a];
+  }
 }
 
 template <int P, typename T>
@@ -1243,8 +1244,6 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
   const bool ina = (code >> 4) & 1u, inb = (code >> 5) & 1u;
   const T *tg = (const T *)tl.geo;
   const T nx = tg[x], ny = tg[tl.n + x], hl = tg[2 * (size_t)tl.n + x];
-  const double hAd = tl.hb[x], hBd = tl.hb[tl.n + x];
-  const T hA = from_d<T>(hAd), hB = from_d<T>(hBd);
   T wa[3][ND];
   tile_modes<P, T>(s_ud, B, s.uin, ne, a, ina, a - e0, wa);
   T ta[NQE][3], hbq[NQE];
@@ -1252,16 +1251,16 @@ __device__ __forceinline__ void tile_edge(const DevMesh &m, const DevTiles &tl, 
   for (int q = 0; q < NQE; ++q) {
 #pragma unroll
     for (int v = 0; v < 3; ++v) ta[q][v] = modal_value<ND, T>(wa[v], s_phe[la][q]);
-    if constexpr (sizeof(T) == sizeof(double))  // h_b at the point (see the area integrals)
-      hbq[q] = ((const T *)tl.hbq)[(size_t)q * tl.n + x];
-    else
-      hbq[q] = T(0.5) * ((T(1) - tb.se[q]) * hA + (T(1) + tb.se[q]) * hB);
+    hbq[q] = ((const T *)tl.hbq)[(size_t)q * tl.n + x];  // h_b at the point, host-computed
   }
   // slot of (element li, local edge l, Gauss point q, variable v)
   auto slot = [&](int li, int l, int q, int v) -> T & { return s_slot[(size_t)((l * NQE + q) * 3 + v) * B + li]; };
   if (b >= 0) {
     const uint8_t fa = s.wd ? (ina ? s_wd[a - e0] : s.wd[a]) : 0;
     const uint8_t fb = s.wd ? (inb ? s_wd[b - e0] : s.wd[b]) : 0;
+    // the edge's vertex depths decide only an edge with exactly one dry side
+    const bool one_dry = (fa == 2) != (fb == 2);
+    const double hAd = one_dry ? tl.hb[x] : 0.0, hBd = one_dry ? tl.hb[tl.n + x] : 0.0;
     const bool flows = edge_flows<P>(ph, fa, fb, s.uin, ne, a, la, b, lb, hAd, hBd);
     if (s.cls) {  // front test: each in-tile side records the other side's flag
       if (ina) s_fr[la * B + a - e0] = fb;
