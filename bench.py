@@ -370,7 +370,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--profile", choices=["storm", "storm-mixed", "shelf", "shelf-mixed", "ensemble-small"],
+    ap.add_argument("--profile", choices=["storm", "storm-mixed", "shelf", "shelf-mixed", "shelf-mixed-p2",
+                                          "ensemble-small"],
                     help="run 3 steps of one workload in a fixed launch configuration (for ncu)")
     ap.add_argument("--variant", type=int, default=1, help="with --profile: 1 split, 2 fused, 3 tiled")
     ap.add_argument("--block", type=int, default=64, help="with --profile: threads per block / tile size")
@@ -399,8 +400,9 @@ def main():
         print(json.dumps({"profile": args.profile, "members": len(members), "steps": 3}))
         return
     if args.profile:
-        mixed = synth.FP32_MIXED if args.profile.endswith("mixed") else synth.FP64
-        case = synth.config3(precision=mixed) if args.profile.startswith("storm") else synth.config2(precision=mixed)
+        mixed = synth.FP32_MIXED if "mixed" in args.profile else synth.FP64
+        p = 2 if args.profile.endswith("p2") else 1
+        case = synth.config3(precision=mixed) if args.profile.startswith("storm") else synth.config2(p=p, precision=mixed)
         m = make_model(case, torch.cuda.Stream(), variant=args.variant, block=args.block)
         m.step(args.profile_steps)
         m.sync()
