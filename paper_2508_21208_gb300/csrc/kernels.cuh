@@ -34,10 +34,12 @@ __device__ __forceinline__ double stage_time(const Clock &c, double tau, double 
 }
 
 // ------------------------------------------------------------------------ conversions
-// double <-> float conversions with integer operations, for the FP64 form's float filters (its
-// kernels are bound by the FP64 pipe, so they keep conversion instructions off it).  The mixed
-// form converts with the hardware instruction (from_d<float>): in its latency-bound kernels that
-// measured 19% faster per storm step than these integer sequences.
+// double <-> float conversions with integer operations.  double -> float (d2f) serves the FP64
+// form's float filters (its kernels are bound by the FP64 pipe, so they keep conversion
+// instructions off it); the mixed form converts double -> float with the hardware instruction
+// (from_d<float>), which in its latency-bound kernels measured 19% faster per storm step than
+// the integer sequence.  float -> double (f2d) serves the mixed form's RK update (to_d<float>),
+// where the hardware widening measured slower.
 // Round-to-nearest-even double -> float for results in float's normal range (same value as the
 // hardware conversion there); smaller magnitudes give a signed zero, larger ones infinity.
 __device__ __forceinline__ float d2f(double x) {
