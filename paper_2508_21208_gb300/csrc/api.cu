@@ -442,6 +442,7 @@ static int capture_one(dgswem_ctx *c, int variant, int block, bool timing) {
   cudaError_t e = cudaStreamEndCapture(c->st, &c->graph);
   if (int r = ctx_cuda(c, e, "end capture")) return r;
   if (int r = ctx_cuda(c, cudaGraphInstantiate(&c->exec, c->graph, 0), "graph instantiate")) return r;
+  c->graph_t0 = c->t0;
   c->variant = variant;
   c->block = block;
   c->timing = timing;
@@ -819,7 +820,9 @@ int dgswem_set_state(dgswem_ctx *c, const double *hz, const double *hqx, const d
   if (c->ph.wetdry)  // recompute the flags only; the state is not modified
     launch_limwd(c->mixed, c->P, false, 2, whole(c->dm), c->U0, c->mean, c->wd, c->ph, c->err, LaunchCfg{128, c->st});
   if (int r = ctx_cuda(c, cudaGetLastError(), "set_state")) return r;
-  // the captured graph bakes t0 into its kernel parameters: recapture
+  // the captured graph bakes t0 into its kernel parameters (the step count comes from the device
+  // counter reset above): recapture only for another t0
+  if (c->exec && c->graph_t0 == t) return 0;
   return capture_graph(c, c->variant, c->block, c->timing);
 }
 

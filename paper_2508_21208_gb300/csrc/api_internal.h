@@ -37,6 +37,7 @@ struct dgswem_ctx {
   int init_kind = 0;  // 0 rest, 1 modal, 2 nodal
   std::vector<double> init_modal, init_nodal;
   double t0 = 0.0, dt = 0.0;
+  double graph_t0 = 0.0;  // the t0 baked into the captured step graph
   int64_t steps_done = 0;
   int nst = 2;  // Runge-Kutta stages
   double ra[dg::MAX_STAGES] = {}, rb[dg::MAX_STAGES] = {}, rc[dg::MAX_STAGES] = {}, rtau[dg::MAX_STAGES] = {};
