@@ -2046,6 +2046,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (P == 1 ? 5 : 2) : 1)) 
   ens_phase<P, T>(a, phase, stage, blockIdx.x, gridDim.x, &sd, s_phe, smem_raw);
 }
 
+// The limiter and wet/dry phase as its own launch (phased mode), without the element phase's
+// shared memory and register needs: the float form runs 6 resident 256-thread blocks per SM, as
+// the single-model limiter does (its gathers' latency wants the warps).
+template <int P, typename T>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 6 : 1)) k_ens_limwd(const EnsArgs a, int stage) {
+  __shared__ MemberDev sd;
+  ens_phase<P, T>(a, 2, stage, blockIdx.x, gridDim.x, &sd, nullptr, nullptr);
+}
+
 template <typename T>
 cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int block, int grid, cudaStream_t s) {
   if (persistent) {
@@ -2078,8 +2087,8 @@ cudaError_t launch_ensemble_t(int p, bool persistent, const EnsArgs &a, int bloc
       }
     }
     if (a.any_limwd) {
-      if (p == 1) k_ens_phase<1, T><<<a.n_etile, block, sm, s>>>(a, 2, stage);
-      else k_ens_phase<2, T><<<a.n_etile, block, sm, s>>>(a, 2, stage);
+      if (p == 1) k_ens_limwd<1, T><<<a.n_etile, block, 0, s>>>(a, stage);
+      else k_ens_limwd<2, T><<<a.n_etile, block, 0, s>>>(a, stage);
     }
   }
   return cudaGetLastError();
