@@ -394,10 +394,11 @@ def main():
         # 8 storms on the 199,712- and 399,618-element meshes (~2.4M elements per stage)
         from paper_2508_21208_gb300 import Ensemble
         meshes, bathys, members = synth.ensemble(members_per_mesh=4, mesh_n=(316, 447))
-        ens = Ensemble(meshes, bathys, members, block=args.block, mode=1, stream=torch.cuda.Stream())
+        mode = 2 if args.variant == 2 else 1  # --variant 2: one launch per phase, else persistent
+        ens = Ensemble(meshes, bathys, members, block=args.block, mode=mode, stream=torch.cuda.Stream())
         ens.step(3)
         ens.sync()
-        print(json.dumps({"profile": args.profile, "members": len(members), "steps": 3}))
+        print(json.dumps({"profile": args.profile, "members": len(members), "steps": 3, "mode": mode}))
         return
     if args.profile:
         mixed = synth.FP32_MIXED if "mixed" in args.profile else synth.FP64
