@@ -31,6 +31,21 @@ def test_recorded_traffic_needs_the_current_sources(tmp_path, monkeypatch):
     assert bench.recorded_traffic("edge_flux", "fp64", 1000, 1) is None
 
 
+def test_ensemble_traffic_follows_the_launch_mode(tmp_path, monkeypatch):
+    """The ensemble's line is a whole step of a smaller batch, scaled per element-stage, and is
+    taken only for the launch mode it was captured in."""
+    sha = bench.kernel_source_sha()
+    _traffic_file(tmp_path, [
+        f"kernel=ensemble_step form=mixed variant=persistent p=1 workload=w elements=1000 bytes=800000 src_sha={sha}",
+        f"kernel=ensemble_step form=mixed variant=phased p=1 workload=w elements=1000 bytes=700000 src_sha={sha}",
+    ])
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: sha)
+    assert bench.recorded_traffic("ensemble_step", "mixed", 3000, "persistent", scale=True) == 2400000
+    assert bench.recorded_traffic("ensemble_step", "mixed", 3000, "phased", scale=True) == 2100000
+    assert bench.recorded_traffic("ensemble_step", "mixed", 3000, "phased") is None  # unscaled: other size
+
+
 def test_recorded_traffic_without_a_summary(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.recorded_traffic("element_update", "fp64", 1000, 3) is None
