@@ -121,6 +121,8 @@ def _case(name):
     if name == "800-triangle hump":
         c = synth.config1(n=20)
         return c, 60
+    if name == "shelf at p=2":
+        return synth.config2(n=20, p=2), 40  # quadratic modes: 6 per variable in each record
     c = synth.config2(n=48)  # 4,608 elements: tide, dry land, wet/dry, limiter, friction
     return c, 60
 
@@ -165,7 +167,7 @@ def _rank_main(rank, world, port, name, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name", ["800-triangle hump", "shelf with dry land"])
+@pytest.mark.parametrize("name", ["800-triangle hump", "shelf with dry land", "shelf at p=2"])
 def test_two_ranks_with_ghost_exchange_equal_single_domain_bitwise(name):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -188,5 +190,5 @@ def test_two_ranks_with_ghost_exchange_equal_single_domain_bitwise(name):
     assert not np.isnan(got_u).any()
     assert np.array_equal(got_u, u)          # bit for bit
     assert np.array_equal(got_f, f)
-    if name == "shelf with dry land":
+    if name != "800-triangle hump":
         assert (f != 0).any() and (f == 0).any()
